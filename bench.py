@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 FEM Fourier solver.
+
+Workload (default): 2D rectangle [0,1]x[0,2], n = 9, K = 1024 x 1024
+(9215^2 = 84,916,225 unknowns), -(1.0 u_xx + 2.5 u_yy) + 1.0 u = f, one seeded
+N(0,1) right-hand side.  One step = one complete solve (all passes of the
+algorithm plus the float64 refinement of the mixed path).  The headline
+``value`` is the mixed-precision solver's DOF/s; the float64 path is timed in
+the same run and reported beside it, with both results' relative error against
+the FP64 CPU oracle at full size when the CPU baseline runs.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (N > 1, launched with torch.distributed.run): independent replicas,
+one right-hand side per rank, no collective on the data path.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FEM DOF/s per solve, mixed vs FP64 on GPU at rel err \u22641e-10; % HBM roofline"
+WORKLOADS = {
+    "2d": dict(name="2d_n9_K1024x1024_X1x2_a1x2.5_c1", n=9, K=(1024, 1024), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
+    "3d": dict(name="3d_n9_K64^3", n=9, K=(64, 64, 64), X=(1.0, 1.0, 1.0), a=(1.0, 1.0, 1.0), c=0.0),
+    "small": dict(name="2d_n2_K16x16", n=2, K=(16, 16), X=(1.0, 1.0), a=(1.0, 1.0), c=0.0),
+}
+FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (profiling recipe table)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def time_steps(torch, fn, steps, warmup, barrier=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def roofline(prof, steps, peaks):
+    """Dominant kernel kind of the step and its achieved fraction of its bound."""
+    kind = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[kind]
+    if p["launches"] == 0 or p["ms"] <= 0:
+        return None, kind
+    per_launch_ms = p["ms"] / p["launches"]
+    if kind == "apply":
+        achieved = p["flops64"] / p["launches"] / (per_launch_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (fp64)",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "apply_kernel (fp64 FMA)",
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table)",
+                "avg_launch_ms": per_launch_ms, "share_of_step": p["ms"] / sum(v["ms"] for v in prof.values())}, kind
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = p["bytes"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": f"pencil_pass_kernel ({kind})",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
+            "avg_launch_ms": per_launch_ms, "share_of_step": p["ms"] / sum(v["ms"] for v in prof.values())}, kind
+
+
+def oracle_full_solve(wl, b):
+    """FP64 oracle solve of the workload on the host cores: (u, seconds of the
+    solve proper, seconds of the eigenbasis)."""
+    from oracle import solve as osolve
+    prob = osolve.Problem(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"])
+    t0 = time.perf_counter()
+    for i in range(prob.N):
+        prob.basis1d(i)
+    prob.denominators()
+    t_basis = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    u = osolve.solve(prob, b)
+    t_solve = time.perf_counter() - t0
+    return u, t_solve, t_basis
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, wl):
+    """Reference arm: the FP64 CPU oracle timed on the host cores.  Each step
+    is one of the four dense axis products of the oracle's solve (a quarter of
+    a solve, cycling), credited with DOF/4."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import solve as osolve
+    from paper_1701_03967_gb300 import synth
+    prob = osolve.Problem(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"])
+    b = synth.normal_field(prob.M, synth.CFG_LARGE_2D if wl["n"] == 9 and len(wl["K"]) == 2 else synth.CFG_TEST)
+    for i in range(prob.N):
+        prob.basis1d(i)
+    D = prob.denominators()
+    stages = []
+    for i in reversed(range(prob.N)):
+        stages.append(("fwd", i))
+    for i in range(prob.N):
+        stages.append(("inv", i))
+    nst = len(stages)
+    state = {"x": b[None], "j": 0}
+
+    def step():
+        kind, i = stages[state["j"] % nst]
+        _, S, cn = prob.basis1d(i)
+        mat = S.T / cn[:, None] if kind == "fwd" else S
+        x = osolve._axis_apply(state["x"], mat, i + 1)
+        if kind == "fwd" and i == 0:
+            x = x / D
+        state["x"] = x if state["j"] % nst != nst - 1 else b[None]
+        state["j"] += 1
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    dof = prob.dof
+    value = dof / nst / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "dof": dof, "nrhs": 1},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores(), "kind": "oracle",
+                             "sample": f"one of the {nst} dense axis products of the oracle solve per step "
+                                       f"(credited DOF/{nst}); eigenbasis precomputed untimed"},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--refine", type=int, default=1, help="refinement steps of the mixed path")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import torch
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    barrier = (lambda: dist.barrier()) if dist else None
+
+    from paper_1701_03967_gb300 import Plan, synth
+    cfg_id = synth.CFG_LARGE_2D if args.workload == "2d" else synth.CFG_TEST
+    mixed = Plan(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"], precision="mixed")
+    mixed.set_refinement(0.0, args.refine)
+    fp64 = Plan(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"], precision="fp64")
+    b_host = synth.normal_field(mixed.M, cfg_id, 0, rank)
+    b = torch.from_numpy(b_host).to(f"cuda:{dev}")
+    u = torch.empty_like(b)
+    u64 = torch.empty_like(b)
+    dof = mixed.dof
+
+    # ---- mixed path (headline), with per-kernel event timing
+    clocks = ClockSampler(dev)
+    for _ in range(args.warmup):
+        mixed.solve(b, out=u)
+    torch.cuda.synchronize()
+    mixed.profile(True)
+    clocks.start()
+    ms_mixed = time_steps(torch, lambda: mixed.solve(b, out=u), args.steps, 0, barrier)
+    clk = clocks.stop()
+    prof = mixed.profile_read()
+    mixed.profile(False)
+    # ---- float64 path in the same run
+    ms_fp64 = time_steps(torch, lambda: fp64.solve(b, out=u64), args.steps, args.warmup, barrier)
+    # ---- end to end through the public API from pinned host memory
+    bh = torch.from_numpy(b_host).pin_memory()
+    uh = torch.empty_like(bh).pin_memory()
+
+    def e2e_step():
+        b.copy_(bh, non_blocking=True)
+        mixed.solve(b, out=u)
+        uh.copy_(u, non_blocking=True)
+    ms_e2e = time_steps(torch, e2e_step, args.steps, args.warmup, barrier)
+
+    if dist:
+        t = torch.tensor([ms_mixed, ms_fp64, ms_e2e], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_mixed, ms_fp64, ms_e2e = (float(x) for x in t.tolist())
+
+    u_mixed = u.cpu().numpy()
+    u_fp64 = u64.cpu().numpy()
+    acc = {"mixed_vs_fp64_rel": float(np.linalg.norm(u_mixed - u_fp64) / np.linalg.norm(u_fp64))}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        u_or, t_solve, t_basis = oracle_full_solve(wl, b_host)
+        nrm = np.linalg.norm(u_or)
+        acc["mixed_rel_err_vs_oracle"] = float(np.linalg.norm(u_mixed - u_or) / nrm)
+        acc["fp64_rel_err_vs_oracle"] = float(np.linalg.norm(u_fp64 - u_or) / nrm)
+        cpu = {"value": dof / t_solve, "unit": "DOF/s", "cores": cores(), "kind": "oracle",
+               "sample": f"one full oracle solve of the workload (dense Theorem-1 eigenbasis products, "
+                         f"{t_solve:.1f} s; eigenbasis {t_basis:.1f} s untimed)"}
+
+    peaks = _peaks()
+    roof, dom = roofline(prof, args.steps, peaks)
+    launches = sum(v["launches"] for v in prof.values()) // max(args.steps, 1)
+    kernels = {k: {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["ms"] / args.steps,
+                   "GB_per_s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else None,
+                   "fp64_TFLOPs": (v["flops64"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] and v["flops64"] else None}
+               for k, v in prof.items()}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": ws * dof / (ms_mixed * 1e-3), "unit": "DOF/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "n": wl["n"], "K": list(wl["K"]), "X": list(wl["X"]),
+                   "a": list(wl["a"]), "c": wl["c"], "dof": dof, "nrhs": 1, "precision": "mixed",
+                   "refine_steps": args.refine, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (b and u 680 MB each, float32 workspace 340 MB)"},
+        "fp64": {"value": ws * dof / (ms_fp64 * 1e-3), "unit": "DOF/s", "ms_per_step": ms_fp64, "dtype": "f64"},
+        "accuracy": acc,
+        "e2e": {"value": ws * dof / (ms_e2e * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": dof * 8,
+                "d2h_bytes_per_step": dof * 8},
+        "roofline": roof,
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

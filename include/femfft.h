@@ -1,0 +1,188 @@
+/*
+ * femfft -- fast direct solver for the tensor-product nth-order FEM
+ * discretisation of a generalised Poisson equation on a rectangular
+ * parallelepiped with homogeneous Dirichlet conditions, on one NVIDIA GB300
+ * (sm_103a).
+ *
+ * Method: A. Zlotnik and I. Zlotnik, "On fast Fourier solvers for the tensor
+ * product high-order FEM for a generalized Poisson equation" (arXiv:1701.03967).
+ *   Problem (Section 4, the N-dimensional boundary value problem and its FEM
+ *   operator form, with per-axis coefficients a_i and zeroth-order term c):
+ *       -sum_i a_i d^2u/dx_i^2 + c u = f  on (0,X_1) x ... x (0,X_N),  u = 0 on the boundary,
+ *       L = sum_i a_i (4/h_i^2) calA_i (x) prod_{j!=i} calC_j + c prod_j calC_j,   L u = b,
+ *   where calA_i, calC_i are the h-free 1D stiffness and mass operators of
+ *   Section 2 (K_i uniform elements of order n on [0, X_i], h_i = X_i / K_i)
+ *   and b is the "FEM average" right-hand side f^h.
+ *   Solve (Section 4, algorithm (a)): direct FC_n-transform along every axis
+ *   (Section 3, Theorem 2, item 2), division by sum_i a_i 4 h_i^-2 lambda_i + c,
+ *   inverse F_n-transform along every axis (Theorem 2, item 1).
+ *
+ * Data layout (all entry points): a field is a C-order array
+ *   [nrhs][M_1][M_2]...[M_N] of float64, M_i = n K_i - 1, axis N contiguous.
+ * Along an axis, index m (0-based) is the FEM node at x = (m+1) h / n: element e
+ * (0-based) owns indices n e .. n e + n - 2 (its interior nodes, l = 1..n-1)
+ * and n e + n - 1 (its right vertex); the two boundary vertices are not stored.
+ * Spectral arrays (fem_fft_forward / fem_fft_inverse) have the same shape;
+ * along an axis, coefficient sigma (0-based) is mode (k, l) with
+ * sigma + 1 = n k + slot: the n-1 bubble modes k = 0 (slot l = 1..n-1) first,
+ * then for k = 1..K-1 the n modes slot = l-1 = 0..n-1 in ascending eigenvalue
+ * order, with the eigenvectors normalised as in Section 3, Theorem 1 (node
+ * values sin(pi k j / K); bubble interiors (-P)^{j-1} e^(l), C~e.e = 1).
+ *
+ * Pointers: every array argument named d_* is a device pointer owned by the
+ * caller (for example a contiguous torch tensor's data_ptr()); h_* arguments
+ * are host pointers.  The library never frees caller memory.  A plan owns its
+ * device tables and workspace.  Streams are passed as cudaStream_t cast to
+ * void* (NULL = legacy default stream).  All calls are asynchronous on that
+ * stream unless stated otherwise; a plan's workspace is shared by all calls
+ * on it, so calls on one plan must be issued on one stream (or serialised).
+ *
+ * nrhs = 0 is a no-op (array pointers may then be NULL).
+ *
+ * Errors: every entry point returns 0 (FEM_FFT_OK) or a negative status.  No
+ * exception crosses the ABI.  An asynchronous device error from an earlier
+ * call surfaces as FEM_FFT_ERR_CUDA at a later synchronising call.
+ */
+#ifndef FEMFFT_H_
+#define FEMFFT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fem_fft_plan_s* fem_fft_plan;
+
+enum fem_fft_status {
+  FEM_FFT_OK = 0,
+  FEM_FFT_ERR_ARG = -1,           /* invalid argument or unsupported size */
+  FEM_FFT_ERR_ASSUMPTION_A = -2,  /* a 1D eigenproblem failed (Section 3, assumption (A)) */
+  FEM_FFT_ERR_OOM = -3,           /* device allocation failed */
+  FEM_FFT_ERR_CUDA = -4,          /* CUDA runtime error (message: fem_fft_last_error) */
+  FEM_FFT_ERR_TIMEOUT = -5,       /* a bounded device wait expired */
+  FEM_FFT_ERR_NOT_CONVERGED = -6, /* refinement stopped above the requested tolerance */
+  FEM_FFT_ERR_NONFINITE = -7      /* NaN or Inf detected in a residual */
+};
+
+enum fem_fft_precision {
+  FEM_FFT_FP64 = 0,  /* transforms, divide and everything else in float64 */
+  FEM_FFT_MIXED = 1  /* float32 transforms + float64 matrix-free residual refinement */
+};
+
+/*
+ * fem_fft_plan_create -- Section 4 (problem statement) and Section 3
+ * (1D eigenpairs, Theorem 1).  Precomputes, on the host in double-double
+ * arithmetic, the reference matrices A, C (Section 2), the bubble eigenpairs
+ * of A~ e = lambda C~ e, for every axis and k = 1..K_i-1 the n eigenpairs
+ * lambda_k^(l), p_k^(l) and norms ||s_k^(l)||_C^2, and the transform tables;
+ * uploads them and allocates the workspace for up to max_nrhs right-hand
+ * sides per call (larger nrhs are processed in groups).  Synchronous.
+ *   N         number of axes, 1..3
+ *   n         element order, 1..9 (the same on every axis)
+ *   h_K[N]    elements per axis; each K_i >= 2 of the form 2^p 3^q with p >= 1
+ *   h_X[N]    axis lengths X_i > 0
+ *   h_a[N]    coefficients a_i > 0
+ *   c         zeroth-order coefficient, c > -pi^2 sum_i a_i / X_i^2 (so L is
+ *             positive definite, Section 4)
+ *   precision FEM_FFT_FP64 or FEM_FFT_MIXED
+ *   max_nrhs  >= 1
+ *   stream    stream for the table uploads
+ * Returns FEM_FFT_ERR_ARG for out-of-range arguments, FEM_FFT_ERR_OOM,
+ * FEM_FFT_ERR_CUDA, or FEM_FFT_ERR_ASSUMPTION_A.  *out is NULL on failure.
+ */
+int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, const double* h_X,
+                        const double* h_a, double c, int precision, int64_t max_nrhs, void* stream);
+
+/* Frees the plan's device tables and workspace (synchronises its stream). */
+int fem_fft_plan_destroy(fem_fft_plan plan);
+
+/*
+ * fem_fft_solve -- u = L^{-1} b, Section 4, algorithm (a).
+ *   d_b, d_u  [nrhs][M_1..M_N] float64; d_b == d_u (in place) is allowed in
+ *             FP64 precision, and in MIXED precision only with refinement
+ *             disabled (max_iter = 0), else FEM_FFT_ERR_ARG.
+ * FP64: 2N-1 pencil passes in float64.  MIXED: the passes in float32, then
+ * max_iter (default 1) refinement steps r = b - L u (float64, matrix-free),
+ * u += L^{-1} r (float32 passes), stopping early when the relative residual
+ * ||r||_2 / ||b||_2 <= rtol (default 0: always take max_iter steps).  The
+ * residual norms are read back at the end of each step only when rtol > 0.
+ */
+int fem_fft_solve(fem_fft_plan plan, const double* d_b, double* d_u, int64_t nrhs, void* stream);
+
+/* fem_fft_apply -- d_b = L d_u in float64, matrix-free (Section 4, operator
+ * form; element blocks of Section 2).  d_u != d_b. */
+int fem_fft_apply(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrhs, void* stream);
+
+/* Refinement controls of the MIXED precision (ignored in FP64). */
+int fem_fft_set_refinement(fem_fft_plan plan, double rtol, int max_iter);
+
+/* Iterations and relative residual ||b - L u|| / ||b|| of the last MIXED
+ * solve whose residual was evaluated (-1 if unknown).  Synchronises. */
+int fem_fft_last_info(fem_fft_plan plan, int* iters, double* rel_residual);
+
+/*
+ * fem_fft_forward -- direct FC_n-transform along every axis (Section 3,
+ * Theorem 2, item 2; Section 4, the multiple expansion of f^h):
+ * d_y (field) -> d_c (spectral coefficients, layout above), float64 path.
+ * fem_fft_inverse -- inverse F_n-transform along every axis (Theorem 2,
+ * item 1): d_c (spectral) -> d_w (field).  d_in may equal d_out.
+ */
+int fem_fft_forward(fem_fft_plan plan, const double* d_y, double* d_c, int64_t nrhs, void* stream);
+int fem_fft_inverse(fem_fft_plan plan, const double* d_c, double* d_w, int64_t nrhs, void* stream);
+
+/*
+ * fem_fft_grad_coeffs -- derivatives of a scalar loss through u = L^{-1} f
+ * with respect to the coefficients (derived from Section 4: dL/da_i =
+ * 4 h_i^-2 calA_i (x) prod_{j!=i} calC_j, dL/dc = prod_j calC_j, so
+ * dloss/da_i = -lam^T (dL/da_i) u and dloss/dc = -lam^T (dL/dc) u with
+ * lam = L^{-1} dloss/du).  Inputs: d_u = L^{-1} f and d_lam = L^{-1} g
+ * (both [nrhs][M..]).  Outputs h_grad_a[N] and *h_grad_c on the host (sums
+ * over all right-hand sides), evaluated matrix-free in float64.  Synchronises.
+ */
+int fem_fft_grad_coeffs(fem_fft_plan plan, const double* d_u, const double* d_lam, int64_t nrhs,
+                        double* h_grad_a, double* h_grad_c, void* stream);
+
+/*
+ * Plan queries (host, synchronous): sizes and the 1D tables of axis i, for
+ * tests.  h_lam/h_cnorm receive M_i values (h-free eigenvalues and C-norms in
+ * the spectral order above); h_p receives K_i * n * (n-1) values: p_k^(l)
+ * for k >= 1 at [k][l-1][:], e^(l) at [0][l-1][:].  Any pointer may be NULL.
+ */
+int fem_fft_plan_dims(fem_fft_plan plan, int* N, int* n, int64_t* h_M, int* precision);
+int fem_fft_axis_tables(fem_fft_plan plan, int axis, double* h_lam, double* h_cnorm, double* h_p);
+
+/*
+ * fem_fft_axis_precompute -- host only (no device call): the 1D tables of
+ * one axis exactly as fem_fft_plan_create computes them (Section 3,
+ * Theorem 1; double-double precompute).  h_lam, h_cnorm: M = nK-1 values in
+ * the spectral order above; h_p: K*n*(n-1) values as in fem_fft_axis_tables.
+ * Any output pointer may be NULL.  Returns FEM_FFT_ERR_ARG for n outside
+ * 1..9 or K outside the supported set, FEM_FFT_ERR_ASSUMPTION_A if an
+ * eigenproblem fails.
+ */
+int fem_fft_axis_precompute(int n, int64_t K, double X, double* h_lam, double* h_cnorm, double* h_p);
+
+/*
+ * Kernel timing (tracing; no paper counterpart).  fem_fft_profile(plan, 1)
+ * starts recording a CUDA event pair around every kernel the plan launches
+ * (on the launch stream), with the algorithmic HBM bytes and float64 flops of
+ * that launch; fem_fft_profile(plan, 0) stops and clears.  Kinds: 0 forward
+ * pencil pass, 1 fused forward/divide/inverse pass, 2 inverse pass,
+ * 3 matrix-free operator apply.  fem_fft_profile_read synchronises and
+ * returns, for one kind, the launch count, summed device milliseconds,
+ * summed algorithmic bytes and float64 flops (any pointer may be NULL).
+ */
+int fem_fft_profile(fem_fft_plan plan, int enable);
+int fem_fft_profile_read(fem_fft_plan plan, int kind, int64_t* launches, double* ms, double* bytes,
+                         double* flops64);
+
+/* Static text for a status code; fem_fft_last_error: the last CUDA error
+ * text recorded by this thread (empty if none). */
+const char* fem_fft_strerror(int code);
+const char* fem_fft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEMFFT_H_ */

@@ -1,0 +1,832 @@
+// C ABI of the solver: plans, pass scheduling, solves, operator apply,
+// refinement and gradient bilinear forms.  Host code.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/femfft.h"
+#include "femfft_internal.h"
+#include "kernels.h"
+#include "pencil.cuh"
+
+using namespace femfft;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return FEM_FFT_ERR_CUDA;
+}
+#define FEMFFT_CUDA(call, what)                      \
+  do {                                               \
+    cudaError_t e_ = (cudaError_t)(call);            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+struct DevTables {
+  void* tw = nullptr;
+  void* rot = nullptr;
+  void* fwd = nullptr;
+  void* inv = nullptr;
+  void* mu = nullptr;
+};
+
+bool valid_K(int64_t K) {
+  if (K < 2 || K > (1 << 20)) return false;
+  if (K % 2) return false;
+  while (K % 2 == 0) K /= 2;
+  while (K % 3 == 0) K /= 3;
+  return K == 1;
+}
+
+// FFT schedule for length K: values per thread V and radix sequence.
+void fft_schedule(int K, int* V, int* npass, int* radix) {
+  int a = 0, b = 0, k = K;
+  while (k % 2 == 0) { k /= 2; ++a; }
+  while (k % 3 == 0) { k /= 3; ++b; }
+  std::vector<int> r;
+  if (b > 0) {
+    for (int i = 0; i < b; ++i) r.push_back(3);
+    int aa = a;
+    if (aa >= 2) {
+      *V = 12;
+      while (aa >= 2) { r.push_back(4); aa -= 2; }
+      if (aa) r.push_back(2);
+    } else {
+      *V = 6;
+      if (aa) r.push_back(2);
+    }
+  } else {
+    if (a >= 3) {
+      *V = 8;
+      int aa = a;
+      while (aa >= 3) { r.push_back(8); aa -= 3; }
+      if (aa == 2) r.push_back(4);
+      if (aa == 1) r.push_back(2);
+    } else {
+      *V = K;          // K = 2 or 4
+      r.push_back(K);
+    }
+  }
+  *npass = (int)r.size();
+  for (size_t i = 0; i < r.size(); ++i) radix[i] = r[i];
+}
+
+}  // namespace
+
+struct fem_fft_plan_s {
+  int N = 0, n = 0, precision = 0;
+  int64_t K[kMaxN] = {0, 0, 0}, M[kMaxN] = {0, 0, 0};
+  double X[kMaxN] = {1, 1, 1}, a[kMaxN] = {1, 1, 1}, c = 0.0;
+  int64_t max_nrhs = 1, dof = 0;
+  AxisHost ax[kMaxN];
+  DevTables t64[kMaxN], t32[kMaxN];
+  std::vector<double> Aref, Cref;      // element matrices
+  float* w32 = nullptr;                // mixed workspace [max_nrhs][dof]
+  double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};   // float64 temporaries
+  double* d_scalars = nullptr;         // device scalars (norms, dots)
+  double rtol = 0.0;
+  int max_iter = 1;
+  int last_iters = -1;
+  double last_rel = -1.0;
+  int smem_optin = 0;
+  std::vector<void*> allocs;
+  // kernel timing (fem_fft_profile)
+  struct ProfRec {
+    cudaEvent_t a, b;
+    int kind;
+    double bytes, flops;
+  };
+  bool profiling = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+int dev_alloc(fem_fft_plan p, void** ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    g_last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return FEM_FFT_ERR_OOM;
+  }
+  p->allocs.push_back(*ptr);
+  return FEM_FFT_OK;
+}
+
+cudaEvent_t pool_event(fem_fft_plan p) {
+  if (!p->event_pool.empty()) {
+    cudaEvent_t e = p->event_pool.back();
+    p->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel launch with an event pair when profiling is on.
+struct ProfScope {
+  fem_fft_plan p;
+  cudaStream_t s;
+  fem_fft_plan_s::ProfRec rec;
+  bool on;
+  ProfScope(fem_fft_plan p_, cudaStream_t s_, int kind, double bytes, double flops) : p(p_), s(s_), on(p_->profiling) {
+    if (!on) return;
+    rec.a = pool_event(p);
+    rec.b = pool_event(p);
+    rec.kind = kind;
+    rec.bytes = bytes;
+    rec.flops = flops;
+    cudaEventRecord(rec.a, s);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(rec.b, s);
+    p->prof.push_back(rec);
+  }
+};
+
+template <typename T>
+int upload(fem_fft_plan p, const std::vector<double>& v, void** dst, cudaStream_t s) {
+  std::vector<T> tmp(v.begin(), v.end());
+  int rc = dev_alloc(p, dst, tmp.size() * sizeof(T));
+  if (rc) return rc;
+  FEMFFT_CUDA(cudaMemcpyAsync(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, s), "upload");
+  FEMFFT_CUDA(cudaStreamSynchronize(s), "upload sync");
+  return FEM_FFT_OK;
+}
+
+template <typename T>
+int upload_axis(fem_fft_plan p, const AxisHost& ax, DevTables* d, cudaStream_t s) {
+  int rc;
+  if ((rc = upload<T>(p, ax.tw, &d->tw, s))) return rc;
+  if ((rc = upload<T>(p, ax.rot, &d->rot, s))) return rc;
+  if ((rc = upload<T>(p, ax.fwd, &d->fwd, s))) return rc;
+  if ((rc = upload<T>(p, ax.inv, &d->inv, s))) return rc;
+  if ((rc = upload<T>(p, ax.mu, &d->mu, s))) return rc;
+  return FEM_FFT_OK;
+}
+
+// ------------------------------------------------------------ pencil passes
+
+struct PassPlan {
+  PassParams P;
+  size_t smem;
+  int threads;
+};
+
+// Pencils per CTA and the CTA grid for a pass over [outer][M][inner].
+int plan_pass(fem_fft_plan p, int axis, long long outer, long long inner, bool f64, PassPlan* pp) {
+  const int n = p->n, K = (int)p->K[axis], M = (int)p->M[axis];
+  const int Q = n / 2 + 1;
+  const size_t csize = f64 ? 2 * sizeof(double) : 2 * sizeof(float);
+  PassParams& P = pp->P;
+  std::memset(&P, 0, sizeof(P));
+  fft_schedule(K, &P.V, &P.npass, P.radix);
+  int pitch = K * Q;
+  if (pitch % 2 == 0) pitch += 1;      // odd pitch spreads pencils over banks
+  P.pitch = pitch;
+  const size_t per_pen = (size_t)pitch * csize;
+  const size_t budget = (size_t)std::min(p->smem_optin, 220 * 1024);
+  long long wmax = (long long)(budget / per_pen);
+  if (wmax < 1) {
+    g_last_error = "pencil does not fit in shared memory";
+    return FEM_FFT_ERR_ARG;
+  }
+  const int threads = kPencilThreads;
+  // chunk tasks of the sequence build: W * K <= kMaxChunkTasks * threads
+  wmax = std::min<long long>(wmax, (long long)kMaxChunkTasks * threads / K);
+  if (wmax < 1 || K / P.V > threads) {
+    g_last_error = "K too large for one CTA";
+    return FEM_FFT_ERR_ARG;
+  }
+  long long W;
+  if (inner == 1) {
+    // keep at least ~2 CTAs per SM when possible
+    long long want = std::max<long long>(1, outer / (2 * 152));
+    W = std::min(wmax, want);
+  } else {
+    W = std::min<long long>(wmax, inner);
+    if (W >= 8) W = W / 8 * 8;
+    long long tiles = outer * ((inner + W - 1) / W);
+    while (W > 1 && tiles < 2 * 152) {
+      W = std::max<long long>(1, W / 2);
+      tiles = outer * ((inner + W - 1) / W);
+    }
+  }
+  P.g.outer = outer;
+  P.g.inner = inner;
+  P.g.M = M;
+  P.g.W = (int)W;
+  if (inner == 1) {
+    P.g.tiles_inner = 1;
+    P.g.tiles = (outer + W - 1) / W;
+  } else {
+    P.g.tiles_inner = (inner + W - 1) / W;
+    P.g.tiles = outer * P.g.tiles_inner;
+  }
+  const DevTables& d = f64 ? p->t64[axis] : p->t32[axis];
+  P.ax.n = n;
+  P.ax.K = K;
+  P.ax.M = M;
+  P.ax.tw = d.tw;
+  P.ax.rot = d.rot;
+  P.ax.fwd = d.fwd;
+  P.ax.inv = d.inv;
+  P.ax.mu = d.mu;
+  pp->smem = (size_t)W * per_pen;
+  pp->threads = threads;
+  return FEM_FFT_OK;
+}
+
+int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const void* in, bool in_f64,
+             void* out, bool out_f64, bool accum, cudaStream_t s) {
+  long long outer = nrhs, inner = 1;
+  for (int j = 0; j < axis; ++j) outer *= p->M[j];
+  for (int j = axis + 1; j < p->N; ++j) inner *= p->M[j];
+  PassPlan pp;
+  int rc = plan_pass(p, axis, outer, inner, f64, &pp);
+  if (rc) return rc;
+  PassParams& P = pp.P;
+  P.in = in;
+  P.out = out;
+  P.in_f64 = in_f64;
+  P.out_f64 = out_f64;
+  P.accum = accum;
+  if (mode == MODE_FUSED) {
+    P.dv.c = p->c;
+    P.dv.nother = p->N - 1;
+    for (int j = 1; j < p->N; ++j) {
+      P.dv.Mo[j - 1] = p->M[j];
+      P.dv.mu_o[j - 1] = f64 ? p->t64[j].mu : p->t32[j].mu;
+    }
+  }
+  const double elems = (double)outer * P.g.M * inner;
+  const double bytes = elems * ((in_f64 ? 8 : 4) + (out_f64 ? 8 : 4) * (accum ? 2 : 1));
+  const int kind = mode == MODE_FWD ? 0 : (mode == MODE_FUSED ? 1 : 2);
+  int e;
+  {
+    ProfScope scope(p, s, kind, bytes, 0.0);
+    e = f64 ? launch_pencil_f64(mode, p->n, P, pp.smem, pp.threads, s)
+            : launch_pencil_f32(mode, p->n, P, pp.smem, pp.threads, s);
+  }
+  if (e) return cuda_fail((cudaError_t)e, "pencil pass launch");
+  return FEM_FFT_OK;
+}
+
+// Algorithm (a): forward passes on axes N-1..1, fused forward/divide/inverse
+// on axis 0, inverse passes on axes 1..N-1.
+int solve_chain(fem_fft_plan p, bool f64, const void* in, bool in_f64, void* work, void* out, bool accum,
+                long long nrhs, cudaStream_t s) {
+  const int N = p->N;
+  int rc;
+  const void* cur = in;
+  bool cur_f64 = in_f64;
+  for (int ax = N - 1; ax >= 1; --ax) {
+    if ((rc = run_pass(p, MODE_FWD, ax, nrhs, f64, cur, cur_f64, work, f64, false, s))) return rc;
+    cur = work;
+    cur_f64 = f64;
+  }
+  // fused pass: the last pass of the chain when N == 1
+  if (N == 1) return run_pass(p, MODE_FUSED, 0, nrhs, f64, cur, cur_f64, out, true, accum, s);
+  if ((rc = run_pass(p, MODE_FUSED, 0, nrhs, f64, cur, cur_f64, work, f64, false, s))) return rc;
+  for (int ax = 1; ax < N; ++ax) {
+    bool last = ax == N - 1;
+    if ((rc = run_pass(p, MODE_INV, ax, nrhs, f64, work, f64, last ? out : work, last ? true : f64,
+                       last ? accum : false, s)))
+      return rc;
+  }
+  return FEM_FFT_OK;
+}
+
+// ----------------------------------------------------------- operator chains
+
+// Algorithmic traffic and float64 flops of one apply launch: every input
+// field read once, every output written once; per output position and term
+// one row of an (n+1)x(n+1) element matrix (two at an element vertex), i.e.
+// 2 (n+1)^2 / n flops per position and term on average.
+int apply_launch(fem_fft_plan p, const ApplyParams& P, cudaStream_t s) {
+  const double elems = (double)P.outer * P.M * P.inner;
+  int nin = 0;
+  for (int i = 0; i < kApplyMaxIn; ++i) nin += P.in[i] != nullptr;
+  double bytes = elems * 8.0 * nin;
+  if (P.dotv) {
+    bytes += elems * 8.0;
+  } else {
+    for (int j = 0; j < P.nout; ++j) bytes += elems * ((j == 0 && P.out0_f32) ? 4.0 : 8.0);
+    if (P.base) bytes += elems * 8.0;
+  }
+  const double n1 = P.n + 1;
+  const double flops = elems * P.nterm * 2.0 * n1 * n1 / P.n;
+  ProfScope scope(p, s, 3, bytes, flops);
+  return launch_apply(P, s);
+}
+
+void set_mat(ApplyParams& A, int t, const std::vector<double>& E, double alpha, const std::vector<double>* E2,
+             double beta, int n1) {
+  for (int i = 0; i < n1 * n1; ++i) A.mats[t][i] = alpha * E[i] + (E2 ? beta * (*E2)[i] : 0.0);
+}
+
+ApplyParams apply_base(fem_fft_plan p, int axis, long long nrhs) {
+  ApplyParams A;
+  std::memset(&A, 0, sizeof(A));
+  long long outer = nrhs, inner = 1;
+  for (int j = 0; j < axis; ++j) outer *= p->M[j];
+  for (int j = axis + 1; j < p->N; ++j) inner *= p->M[j];
+  A.outer = outer;
+  A.inner = inner;
+  A.M = (int)p->M[axis];
+  A.n = p->n;
+  A.K = (int)p->K[axis];
+  return A;
+}
+
+// kind 0: out = L u (float64);  kind 1: r = b - L u (float32 into r32, norms
+// optional);  the temporaries p->tmp hold the partial products.
+int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, double* out, const double* b,
+                   float* r32, double* norms, cudaStream_t s) {
+  const int N = p->N, n1 = p->n + 1;
+  const std::vector<double>& A = p->Aref;
+  const std::vector<double>& C = p->Cref;
+  double s_[kMaxN];
+  for (int i = 0; i < N; ++i) s_[i] = p->a[i] * 4.0 * p->K[i] * p->K[i] / (p->X[i] * p->X[i]);
+  auto finish = [&](ApplyParams& P) {
+    if (kind == 0) {
+      P.out[0] = out;
+    } else {
+      P.base = b;
+      P.out0_f32 = r32;
+      P.norms = norms;
+    }
+  };
+  int e;
+  if (N == 1) {
+    ApplyParams P = apply_base(p, 0, nrhs);
+    P.in[0] = u;
+    P.nterm = 1;
+    P.nout = 1;
+    set_mat(P, 0, A, s_[0], &C, p->c, n1);
+    finish(P);
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+    return FEM_FFT_OK;
+  }
+  if (N == 2) {
+    ApplyParams P = apply_base(p, 1, nrhs);       // t1 = C2 u, t2 = A2 u
+    P.in[0] = u;
+    P.nterm = 2;
+    P.nout = 2;
+    P.out[0] = p->tmp[0];
+    P.out[1] = p->tmp[1];
+    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1);
+    P.t_src[0] = 0; P.t_dst[0] = 0;
+    set_mat(P, 1, A, s_[1], nullptr, 0.0, n1);
+    P.t_src[1] = 0; P.t_dst[1] = 1;
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+    ApplyParams Q = apply_base(p, 0, nrhs);       // (a1 s1 A1 + c C1) t1 + C1 t2
+    Q.in[0] = p->tmp[0];
+    Q.in[1] = p->tmp[1];
+    Q.nterm = 2;
+    Q.nout = 1;
+    set_mat(Q, 0, A, s_[0], &C, p->c, n1);
+    Q.t_src[0] = 0; Q.t_dst[0] = 0;
+    set_mat(Q, 1, C, 1.0, nullptr, 0.0, n1);
+    Q.t_src[1] = 1; Q.t_dst[1] = 0;
+    finish(Q);
+    if ((e = apply_launch(p, Q, s))) return cuda_fail((cudaError_t)e, "apply");
+    return FEM_FFT_OK;
+  }
+  // N == 3: t = C3 u, v = A3 u; w1 = C2 t, w2 = a2 s2 A2 t + a3 s3 C2 v;
+  // L u = (a1 s1 A1 + c C1) w1 + C1 w2
+  ApplyParams P = apply_base(p, 2, nrhs);
+  P.in[0] = u;
+  P.nterm = 2;
+  P.nout = 2;
+  P.out[0] = p->tmp[0];
+  P.out[1] = p->tmp[1];
+  set_mat(P, 0, C, 1.0, nullptr, 0.0, n1);
+  P.t_src[0] = 0; P.t_dst[0] = 0;
+  set_mat(P, 1, A, 1.0, nullptr, 0.0, n1);
+  P.t_src[1] = 0; P.t_dst[1] = 1;
+  if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+  ApplyParams Q = apply_base(p, 1, nrhs);
+  Q.in[0] = p->tmp[0];
+  Q.in[1] = p->tmp[1];
+  Q.nterm = 3;
+  Q.nout = 2;
+  Q.out[0] = p->tmp[2];
+  Q.out[1] = p->tmp[3];
+  set_mat(Q, 0, C, 1.0, nullptr, 0.0, n1);
+  Q.t_src[0] = 0; Q.t_dst[0] = 0;
+  set_mat(Q, 1, A, s_[1], nullptr, 0.0, n1);
+  Q.t_src[1] = 0; Q.t_dst[1] = 1;
+  set_mat(Q, 2, C, s_[2], nullptr, 0.0, n1);
+  Q.t_src[2] = 1; Q.t_dst[2] = 1;
+  if ((e = apply_launch(p, Q, s))) return cuda_fail((cudaError_t)e, "apply");
+  ApplyParams R = apply_base(p, 0, nrhs);
+  R.in[0] = p->tmp[2];
+  R.in[1] = p->tmp[3];
+  R.nterm = 2;
+  R.nout = 1;
+  set_mat(R, 0, A, s_[0], &C, p->c, n1);
+  R.t_src[0] = 0; R.t_dst[0] = 0;
+  set_mat(R, 1, C, 1.0, nullptr, 0.0, n1);
+  R.t_src[1] = 1; R.t_dst[1] = 0;
+  finish(R);
+  if ((e = apply_launch(p, R, s))) return cuda_fail((cudaError_t)e, "apply");
+  return FEM_FFT_OK;
+}
+
+// dots[i] += lam^T (dL/da_i) u (i < N), dots[N] += lam^T (dL/dc) u
+int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrhs, double* dots, cudaStream_t s) {
+  const int N = p->N, n1 = p->n + 1;
+  const std::vector<double>& A = p->Aref;
+  const std::vector<double>& C = p->Cref;
+  double s_[kMaxN];
+  for (int i = 0; i < N; ++i) s_[i] = 4.0 * p->K[i] * p->K[i] / (p->X[i] * p->X[i]);
+  int e;
+  if (N == 1) {
+    ApplyParams P = apply_base(p, 0, nrhs);
+    P.in[0] = u;
+    P.nterm = 2;
+    P.nout = 2;
+    set_mat(P, 0, A, s_[0], nullptr, 0.0, n1);
+    P.t_src[0] = 0; P.t_dst[0] = 0;
+    set_mat(P, 1, C, 1.0, nullptr, 0.0, n1);
+    P.t_src[1] = 0; P.t_dst[1] = 1;
+    P.dotv = lam;
+    P.dots = dots;
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+    return FEM_FFT_OK;
+  }
+  if (N == 2) {
+    ApplyParams P = apply_base(p, 1, nrhs);       // t1 = C2 u, t2 = A2 u
+    P.in[0] = u;
+    P.nterm = 2;
+    P.nout = 2;
+    P.out[0] = p->tmp[0];
+    P.out[1] = p->tmp[1];
+    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1);
+    P.t_src[0] = 0; P.t_dst[0] = 0;
+    set_mat(P, 1, A, 1.0, nullptr, 0.0, n1);
+    P.t_src[1] = 0; P.t_dst[1] = 1;
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+    ApplyParams Q = apply_base(p, 0, nrhs);       // s1 A1 t1, s2 C1 t2, C1 t1
+    Q.in[0] = p->tmp[0];
+    Q.in[1] = p->tmp[1];
+    Q.nterm = 3;
+    Q.nout = 3;
+    set_mat(Q, 0, A, s_[0], nullptr, 0.0, n1);
+    Q.t_src[0] = 0; Q.t_dst[0] = 0;
+    set_mat(Q, 1, C, s_[1], nullptr, 0.0, n1);
+    Q.t_src[1] = 1; Q.t_dst[1] = 1;
+    set_mat(Q, 2, C, 1.0, nullptr, 0.0, n1);
+    Q.t_src[2] = 0; Q.t_dst[2] = 2;
+    Q.dotv = lam;
+    Q.dots = dots;
+    if ((e = apply_launch(p, Q, s))) return cuda_fail((cudaError_t)e, "apply");
+    return FEM_FFT_OK;
+  }
+  ApplyParams P = apply_base(p, 2, nrhs);         // t = C3 u, v = A3 u
+  P.in[0] = u;
+  P.nterm = 2;
+  P.nout = 2;
+  P.out[0] = p->tmp[0];
+  P.out[1] = p->tmp[1];
+  set_mat(P, 0, C, 1.0, nullptr, 0.0, n1);
+  P.t_src[0] = 0; P.t_dst[0] = 0;
+  set_mat(P, 1, A, 1.0, nullptr, 0.0, n1);
+  P.t_src[1] = 0; P.t_dst[1] = 1;
+  if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+  ApplyParams Q = apply_base(p, 1, nrhs);         // w1 = C2 t, w2 = A2 t
+  Q.in[0] = p->tmp[0];
+  Q.nterm = 2;
+  Q.nout = 2;
+  Q.out[0] = p->tmp[2];
+  Q.out[1] = p->tmp[3];
+  set_mat(Q, 0, C, 1.0, nullptr, 0.0, n1);
+  Q.t_src[0] = 0; Q.t_dst[0] = 0;
+  set_mat(Q, 1, A, 1.0, nullptr, 0.0, n1);
+  Q.t_src[1] = 0; Q.t_dst[1] = 1;
+  if ((e = apply_launch(p, Q, s))) return cuda_fail((cudaError_t)e, "apply");
+  ApplyParams Q3 = apply_base(p, 1, nrhs);        // w3 = C2 v into tmp[0] (t is dead now)
+  Q3.in[0] = p->tmp[1];
+  Q3.nterm = 1;
+  Q3.nout = 1;
+  Q3.out[0] = p->tmp[0];
+  set_mat(Q3, 0, C, 1.0, nullptr, 0.0, n1);
+  Q3.t_src[0] = 0; Q3.t_dst[0] = 0;
+  if ((e = apply_launch(p, Q3, s))) return cuda_fail((cudaError_t)e, "apply");
+  ApplyParams R = apply_base(p, 0, nrhs);         // s1 A1 w1, s2 C1 w2, s3 C1 w3, C1 w1
+  R.in[0] = p->tmp[2];
+  R.in[1] = p->tmp[3];
+  R.in[2] = p->tmp[0];
+  R.nterm = 4;
+  R.nout = 4;
+  set_mat(R, 0, A, s_[0], nullptr, 0.0, n1);
+  R.t_src[0] = 0; R.t_dst[0] = 0;
+  set_mat(R, 1, C, s_[1], nullptr, 0.0, n1);
+  R.t_src[1] = 1; R.t_dst[1] = 1;
+  set_mat(R, 2, C, s_[2], nullptr, 0.0, n1);
+  R.t_src[2] = 2; R.t_dst[2] = 2;
+  set_mat(R, 3, C, 1.0, nullptr, 0.0, n1);
+  R.t_src[3] = 0; R.t_dst[3] = 3;
+  R.dotv = lam;
+  R.dots = dots;
+  if ((e = apply_launch(p, R, s))) return cuda_fail((cudaError_t)e, "apply");
+  return FEM_FFT_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char* fem_fft_strerror(int code) {
+  switch (code) {
+    case FEM_FFT_OK: return "ok";
+    case FEM_FFT_ERR_ARG: return "invalid argument";
+    case FEM_FFT_ERR_ASSUMPTION_A: return "1D eigenproblem failed (assumption (A))";
+    case FEM_FFT_ERR_OOM: return "device out of memory";
+    case FEM_FFT_ERR_CUDA: return "CUDA error";
+    case FEM_FFT_ERR_TIMEOUT: return "device wait timed out";
+    case FEM_FFT_ERR_NOT_CONVERGED: return "refinement did not converge";
+    case FEM_FFT_ERR_NONFINITE: return "non-finite residual";
+    default: return "unknown status";
+  }
+}
+
+const char* fem_fft_last_error(void) { return g_last_error.c_str(); }
+
+int fem_fft_plan_destroy(fem_fft_plan p) {
+  if (!p) return FEM_FFT_ERR_ARG;
+  cudaDeviceSynchronize();
+  for (void* ptr : p->allocs) cudaFree(ptr);
+  for (auto& r : p->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+  delete p;
+  return FEM_FFT_OK;
+}
+
+int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, const double* h_X,
+                        const double* h_a, double c, int precision, int64_t max_nrhs, void* stream) {
+  if (!out) return FEM_FFT_ERR_ARG;
+  *out = nullptr;
+  if (N < 1 || N > kMaxN || n < 1 || n > kMaxOrder || !h_K || !h_X || !h_a || max_nrhs < 1) {
+    g_last_error = "argument out of range";
+    return FEM_FFT_ERR_ARG;
+  }
+  if (precision != FEM_FFT_FP64 && precision != FEM_FFT_MIXED) return FEM_FFT_ERR_ARG;
+  double cmin = 0.0;
+  for (int i = 0; i < N; ++i) {
+    if (!valid_K(h_K[i]) || !(h_X[i] > 0.0) || !(h_a[i] > 0.0) || !std::isfinite(h_X[i]) ||
+        !std::isfinite(h_a[i])) {
+      g_last_error = "K must be 2^p 3^q (p >= 1), X_i and a_i positive";
+      return FEM_FFT_ERR_ARG;
+    }
+    cmin -= M_PI * M_PI * h_a[i] / (h_X[i] * h_X[i]);
+  }
+  if (!std::isfinite(c) || !(c > cmin)) {
+    g_last_error = "c must exceed -pi^2 sum a_i / X_i^2";
+    return FEM_FFT_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  fem_fft_plan p = new (std::nothrow) fem_fft_plan_s();
+  if (!p) return FEM_FFT_ERR_OOM;
+  p->N = N;
+  p->n = n;
+  p->precision = precision;
+  p->c = c;
+  p->max_nrhs = max_nrhs;
+  p->dof = 1;
+  for (int i = 0; i < N; ++i) {
+    p->K[i] = h_K[i];
+    p->X[i] = h_X[i];
+    p->a[i] = h_a[i];
+    p->M[i] = n * h_K[i] - 1;
+    p->dof *= p->M[i];
+  }
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (ce != cudaSuccess) {
+    delete p;
+    return cuda_fail(ce, "device query");
+  }
+  int rc = FEM_FFT_OK;
+  reference_matrices(n, &p->Aref, &p->Cref);
+  for (int i = 0; i < N && !rc; ++i) {
+    // identical axes share nothing on purpose: tables are small
+    if (precompute_axis(n, (int)p->K[i], p->X[i], p->a[i], &p->ax[i])) rc = FEM_FFT_ERR_ASSUMPTION_A;
+  }
+  for (int i = 0; i < N && !rc; ++i) rc = upload_axis<double>(p, p->ax[i], &p->t64[i], s);
+  if (precision == FEM_FFT_MIXED)
+    for (int i = 0; i < N && !rc; ++i) rc = upload_axis<float>(p, p->ax[i], &p->t32[i], s);
+  const size_t field = (size_t)max_nrhs * p->dof;
+  if (!rc && precision == FEM_FFT_MIXED) rc = dev_alloc(p, (void**)&p->w32, field * sizeof(float));
+  const int ntmp = N == 1 ? 0 : (N == 2 ? 2 : 4);
+  for (int t = 0; t < ntmp && !rc; ++t) rc = dev_alloc(p, (void**)&p->tmp[t], field * sizeof(double));
+  if (!rc) rc = dev_alloc(p, (void**)&p->d_scalars, 16 * sizeof(double));
+  if (rc) {
+    for (void* ptr : p->allocs) cudaFree(ptr);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return FEM_FFT_OK;
+}
+
+int fem_fft_set_refinement(fem_fft_plan p, double rtol, int max_iter) {
+  if (!p || rtol < 0.0 || max_iter < 0) return FEM_FFT_ERR_ARG;
+  p->rtol = rtol;
+  p->max_iter = max_iter;
+  return FEM_FFT_OK;
+}
+
+int fem_fft_last_info(fem_fft_plan p, int* iters, double* rel) {
+  if (!p) return FEM_FFT_ERR_ARG;
+  if (iters) *iters = p->last_iters;
+  if (rel) *rel = p->last_rel;
+  return FEM_FFT_OK;
+}
+
+int fem_fft_plan_dims(fem_fft_plan p, int* N, int* n, int64_t* h_M, int* precision) {
+  if (!p) return FEM_FFT_ERR_ARG;
+  if (N) *N = p->N;
+  if (n) *n = p->n;
+  if (precision) *precision = p->precision;
+  if (h_M)
+    for (int i = 0; i < p->N; ++i) h_M[i] = p->M[i];
+  return FEM_FFT_OK;
+}
+
+int fem_fft_axis_tables(fem_fft_plan p, int axis, double* h_lam, double* h_cnorm, double* h_p) {
+  if (!p || axis < 0 || axis >= p->N) return FEM_FFT_ERR_ARG;
+  const AxisHost& ax = p->ax[axis];
+  if (h_lam) std::memcpy(h_lam, ax.lam.data(), ax.lam.size() * sizeof(double));
+  if (h_cnorm) std::memcpy(h_cnorm, ax.cnorm.data(), ax.cnorm.size() * sizeof(double));
+  if (h_p && p->n > 1) std::memcpy(h_p, ax.pvec.data(), (size_t)ax.K * ax.n * (ax.n - 1) * sizeof(double));
+  return FEM_FFT_OK;
+}
+
+int fem_fft_axis_precompute(int n, int64_t K, double X, double* h_lam, double* h_cnorm, double* h_p) {
+  if (n < 1 || n > kMaxOrder || !valid_K(K) || !(X > 0.0)) return FEM_FFT_ERR_ARG;
+  AxisHost ax;
+  if (precompute_axis(n, (int)K, X, 1.0, &ax)) return FEM_FFT_ERR_ASSUMPTION_A;
+  if (h_lam) std::memcpy(h_lam, ax.lam.data(), ax.lam.size() * sizeof(double));
+  if (h_cnorm) std::memcpy(h_cnorm, ax.cnorm.data(), ax.cnorm.size() * sizeof(double));
+  if (h_p && n > 1) std::memcpy(h_p, ax.pvec.data(), (size_t)K * n * (n - 1) * sizeof(double));
+  return FEM_FFT_OK;
+}
+
+int fem_fft_profile(fem_fft_plan p, int enable) {
+  if (!p) return FEM_FFT_ERR_ARG;
+  if (!enable) {
+    cudaDeviceSynchronize();
+    for (auto& r : p->prof) {
+      p->event_pool.push_back(r.a);
+      p->event_pool.push_back(r.b);
+    }
+    p->prof.clear();
+  }
+  p->profiling = enable != 0;
+  return FEM_FFT_OK;
+}
+
+int fem_fft_profile_read(fem_fft_plan p, int kind, int64_t* launches, double* ms, double* bytes, double* flops) {
+  if (!p || kind < 0 || kind > 3) return FEM_FFT_ERR_ARG;
+  int64_t cnt = 0;
+  double t = 0, by = 0, fl = 0;
+  for (auto& r : p->prof) {
+    if (r.kind != kind) continue;
+    FEMFFT_CUDA(cudaEventSynchronize(r.b), "profile sync");
+    float dt = 0.f;
+    FEMFFT_CUDA(cudaEventElapsedTime(&dt, r.a, r.b), "profile elapsed");
+    ++cnt;
+    t += dt;
+    by += r.bytes;
+    fl += r.flops;
+  }
+  if (launches) *launches = cnt;
+  if (ms) *ms = t;
+  if (bytes) *bytes = by;
+  if (flops) *flops = fl;
+  return FEM_FFT_OK;
+}
+
+int fem_fft_solve(fem_fft_plan p, const double* b, double* u, int64_t nrhs, void* stream) {
+  if (p && nrhs == 0) return FEM_FFT_OK;   // nothing to do (pointers may be NULL)
+  if (!p || !b || !u || nrhs < 0) return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool mixed = p->precision == FEM_FFT_MIXED;
+  if (mixed && b == u && p->max_iter > 0) {
+    g_last_error = "in-place mixed-precision solve needs max_iter = 0";
+    return FEM_FFT_ERR_ARG;
+  }
+  int rc;
+  for (int64_t r0 = 0; r0 < nrhs; r0 += p->max_nrhs) {
+    const long long cnt = std::min<int64_t>(p->max_nrhs, nrhs - r0);
+    const double* bb = b + (size_t)r0 * p->dof;
+    double* uu = u + (size_t)r0 * p->dof;
+    if (!mixed) {
+      if ((rc = solve_chain(p, true, bb, true, uu, uu, false, cnt, s))) return rc;
+      continue;
+    }
+    if ((rc = solve_chain(p, false, bb, true, p->w32, uu, false, cnt, s))) return rc;
+    p->last_iters = 0;
+    p->last_rel = -1.0;
+    for (int it = 0; it < p->max_iter; ++it) {
+      double* norms = nullptr;
+      if (p->rtol > 0.0) {
+        FEMFFT_CUDA(cudaMemsetAsync(p->d_scalars, 0, 2 * sizeof(double), s), "memset");
+        norms = p->d_scalars;
+      }
+      if ((rc = operator_chain(p, uu, cnt, 1, nullptr, bb, p->w32, norms, s))) return rc;
+      if (norms) {
+        double h[2];
+        FEMFFT_CUDA(cudaMemcpyAsync(h, p->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, s), "norms");
+        FEMFFT_CUDA(cudaStreamSynchronize(s), "norms sync");
+        if (!std::isfinite(h[0])) return FEM_FFT_ERR_NONFINITE;
+        p->last_rel = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+        if (p->last_rel <= p->rtol) break;
+      }
+      if ((rc = solve_chain(p, false, p->w32, false, p->w32, uu, true, cnt, s))) return rc;
+      p->last_iters = it + 1;
+    }
+  }
+  return FEM_FFT_OK;
+}
+
+int fem_fft_apply(fem_fft_plan p, const double* u, double* b, int64_t nrhs, void* stream) {
+  if (p && nrhs == 0) return FEM_FFT_OK;   // nothing to do (pointers may be NULL)
+  if (!p || !u || !b || u == b || nrhs < 0) return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  for (int64_t r0 = 0; r0 < nrhs; r0 += p->max_nrhs) {
+    const long long cnt = std::min<int64_t>(p->max_nrhs, nrhs - r0);
+    if ((rc = operator_chain(p, u + (size_t)r0 * p->dof, cnt, 0, b + (size_t)r0 * p->dof, nullptr, nullptr,
+                             nullptr, s)))
+      return rc;
+  }
+  return FEM_FFT_OK;
+}
+
+int fem_fft_forward(fem_fft_plan p, const double* y, double* c, int64_t nrhs, void* stream) {
+  if (p && nrhs == 0) return FEM_FFT_OK;   // nothing to do (pointers may be NULL)
+  if (!p || !y || !c || nrhs < 0) return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  for (int ax = p->N - 1; ax >= 0; --ax) {
+    if ((rc = run_pass(p, MODE_FWD, ax, nrhs, true, ax == p->N - 1 ? (const void*)y : (const void*)c, true, c,
+                       true, false, s)))
+      return rc;
+  }
+  return FEM_FFT_OK;
+}
+
+int fem_fft_inverse(fem_fft_plan p, const double* c, double* w, int64_t nrhs, void* stream) {
+  if (p && nrhs == 0) return FEM_FFT_OK;   // nothing to do (pointers may be NULL)
+  if (!p || !c || !w || nrhs < 0) return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  for (int ax = 0; ax < p->N; ++ax) {
+    if ((rc = run_pass(p, MODE_INV, ax, nrhs, true, ax == 0 ? (const void*)c : (const void*)w, true, w, true,
+                       false, s)))
+      return rc;
+  }
+  return FEM_FFT_OK;
+}
+
+int fem_fft_grad_coeffs(fem_fft_plan p, const double* u, const double* lam, int64_t nrhs, double* h_grad_a,
+                        double* h_grad_c, void* stream) {
+  if (!p || !u || !lam || !h_grad_a || !h_grad_c || nrhs < 0) return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  FEMFFT_CUDA(cudaMemsetAsync(p->d_scalars, 0, 8 * sizeof(double), s), "memset");
+  int rc;
+  for (int64_t r0 = 0; r0 < nrhs; r0 += p->max_nrhs) {
+    const long long cnt = std::min<int64_t>(p->max_nrhs, nrhs - r0);
+    if ((rc = grad_chain(p, u + (size_t)r0 * p->dof, lam + (size_t)r0 * p->dof, cnt, p->d_scalars, s))) return rc;
+  }
+  double h[8];
+  FEMFFT_CUDA(cudaMemcpyAsync(h, p->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, s), "dots");
+  FEMFFT_CUDA(cudaStreamSynchronize(s), "dots sync");
+  for (int i = 0; i < p->N; ++i) h_grad_a[i] = -h[i];
+  *h_grad_c = -h[p->N];
+  return FEM_FFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,43 @@
+// Host-side declarations of the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "femfft_internal.h"
+
+namespace femfft {
+
+struct PassParams;
+
+// pencil passes (pencil_f64.cu / pencil_f32.cu): mode 0 forward, 1 inverse,
+// 2 fused forward/divide/inverse.  Returns a cudaError_t value.
+int launch_pencil_f64(int mode, int n, const PassParams& P, size_t smem, int threads, cudaStream_t s);
+int launch_pencil_f32(int mode, int n, const PassParams& P, size_t smem, int threads, cudaStream_t s);
+
+// Matrix-free float64 application of element-block operators along one axis
+// (apply.cu).  Every term adds mats[t] (an (n+1)x(n+1) element matrix,
+// row-major) applied along the axis to input src[t] into output dst[t].
+constexpr int kApplyMaxTerms = 4;
+constexpr int kApplyMaxIn = 3;
+constexpr int kApplyMaxOut = 4;
+constexpr int kApplyMatMax = (kMaxOrder + 1) * (kMaxOrder + 1);
+
+struct ApplyParams {
+  const double* in[kApplyMaxIn];
+  double* out[kApplyMaxOut];     // float64 outputs (unused in dot mode)
+  int nterm, nout;
+  int t_src[kApplyMaxTerms], t_dst[kApplyMaxTerms];
+  double mats[kApplyMaxTerms][kApplyMatMax];
+  // residual form for output 0: out0 = base - sum (base != null)
+  const double* base;
+  float* out0_f32;               // if set, output 0 is written as float32 here
+  double* norms;                 // if set: += ||out0||^2 (norms[0]), ||base||^2 (norms[1])
+  // dot mode: dots[o] += sum_i dotv[i] * out_o[i]; nothing is written
+  const double* dotv;
+  double* dots;
+  long long outer, inner;
+  int M, n, K;
+};
+
+int launch_apply(const ApplyParams& P, cudaStream_t s);
+
+}  // namespace femfft

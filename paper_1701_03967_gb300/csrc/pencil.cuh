@@ -1,0 +1,584 @@
+// Pencil-pass kernels: the direct FC_n-transform, the inverse F_n-transform
+// and the fused forward / spectral-divide / inverse pass along one axis.
+//
+// Method (Zlotnik & Zlotnik, arXiv:1701.03967, Section 3, Theorem 2 and
+// Section 4, algorithm (a)).  For one pencil y in S_K^(n) (node values y_j,
+// j = 1..K-1, and element-interior vectors y_{j-1/2} in R^{n-1}) the FC_n
+// coefficient of mode (k, l), k >= 1, is (Theorem 2, item 2)
+//     y~_kl = [ sum_j y_j sin(pi k j/K)
+//             + sum_j y_{j-1/2} . (p sin(pi k (j-1)/K) + flip(p) sin(pi k j/K)) ] / N_kl,
+// with p = p_k^(l) and N_kl = ||s_k^(l)||_C^2.  With phi_k = pi k / (2K) and
+// the half-sample angles pi k (j - 1/2) / K, the identity used in the proof
+// of Theorem 2 gives
+//     p sin(pi k (j-1)/K) + flip(p) sin(pi k j/K)
+//         = 2 cos(phi_k) p_e sin(pi k (j-1/2)/K) - 2 sin(phi_k) p_o cos(pi k (j-1/2)/K),
+// and the node sum is rewritten the same way through the sum and the
+// difference of the two nodes of each element:
+//     sum_j y_j sin(pi k j/K) = 1/2 cos(phi_k) DST2(y_j + y_{j-1})_k
+//                               + 1/2 sin(phi_k) DCT2(y_j - y_{j-1})_k.
+// So every coefficient needs only half-sample sine (DST-II) and cosine
+// (DCT-II) sums of n+1 real sequences per pencil: the node sum and
+// difference, and the even/odd combinations y[m] +- y[n-m] of the interiors.
+// The bubble modes (k = 0, Theorem 2, item 2, first formula) are the same
+// sums at frequency K (sine: alternating sum) and 0 (cosine: plain sum).
+// The inverse F_n-transform (Theorem 2, item 1) is the transpose structure:
+// node values by a DST-III plus DCT-III of sigma_k = sum_l w_kl weighted by
+// cos(phi_k) / sin(phi_k), interiors by the DST-III of 2cos(phi_k) d_{k,e}
+// and the DCT-III of -2 sin(phi_k) d_{k,o} (d_k = sum_l w_kl p_k^(l)), the
+// bubble term entering as the k = K sine and k = 0 cosine coefficients.
+//
+// GPU mapping.  A sine sequence (modulated by (-1)^j) and a cosine sequence
+// are packed as the real and imaginary parts of one complex sequence of
+// length K; one complex FFT of length K then yields both DCT-II (Makhoul's
+// even/odd reordering and a post-twiddle by exp(-i phi_k) combining bins k and
+// K-k), and likewise for DCT-III (pre-twiddle, FFT, un-reordering).  A CTA
+// holds W whole pencils in shared memory (chunk e of a pencil = element e,
+// 2Q reals), builds the Q = floor(n/2)+1 complex sequences in place, runs a
+// mixed-radix (2,3,4,8) Stockham FFT with the reorderings folded into the
+// first/last pass addressing, and applies the per-frequency n x (n+1) maps
+// with one thread per frequency pair (k, K-k).  Everything between the HBM
+// load and the HBM store stays in shared memory.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "femfft_internal.h"
+
+namespace femfft {
+
+template <typename T>
+struct cpx {
+  T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+// multiply by -i
+template <typename T>
+__device__ __forceinline__ cpx<T> cmi(cpx<T> a) { return {a.im, -a.re}; }
+
+template <typename T>
+__device__ __forceinline__ cpx<T> ld_cpx(const void* base, int idx) {
+  const T* p = reinterpret_cast<const T*>(base) + 2 * idx;
+  return {__ldg(p), __ldg(p + 1)};
+}
+
+enum PassMode { MODE_FWD = 0, MODE_INV = 1, MODE_FUSED = 2 };
+
+constexpr int kMaxV = 12;          // FFT values held per thread
+constexpr int kMaxChunkTasks = 16; // chunks per thread in the sequence build
+constexpr int kMaxRadixPasses = 16;
+constexpr int kPencilThreads = 256; // threads per CTA of the pencil passes
+
+struct PassParams {
+  const void* in;
+  void* out;
+  PassGeom g;
+  AxisDev ax;
+  DivideDev dv;
+  int pitch;         // complex elements per pencil in shared memory
+  int V;             // FFT values per thread
+  int npass;
+  int radix[kMaxRadixPasses];
+  int in_f64, out_f64, accum;
+};
+
+// ------------------------------------------------------------- radix DFTs
+// forward DFT, omega = exp(-2 pi i / R)
+
+template <typename T>
+__device__ __forceinline__ void dft2(cpx<T>* u) {
+  cpx<T> a = u[0], b = u[1];
+  u[0] = cadd(a, b);
+  u[1] = csub(a, b);
+}
+template <typename T>
+__device__ __forceinline__ void dft4(cpx<T>* u) {
+  cpx<T> t0 = cadd(u[0], u[2]), t1 = csub(u[0], u[2]);
+  cpx<T> t2 = cadd(u[1], u[3]), t3 = cmi(csub(u[1], u[3]));
+  u[0] = cadd(t0, t2);
+  u[2] = csub(t0, t2);
+  u[1] = cadd(t1, t3);
+  u[3] = csub(t1, t3);
+}
+template <typename T>
+__device__ __forceinline__ void dft3(cpx<T>* u) {
+  const T h = T(0.5), s3 = T(0.86602540378443864676372317075294);   // sqrt(3)/2
+  cpx<T> t = cadd(u[1], u[2]), d = csub(u[1], u[2]);
+  cpx<T> m = {u[0].re - h * t.re, u[0].im - h * t.im};
+  cpx<T> r = {s3 * d.im, -s3 * d.re};   // -i sqrt(3)/2 d
+  u[0] = cadd(u[0], t);
+  u[1] = cadd(m, r);
+  u[2] = csub(m, r);
+}
+template <typename T>
+__device__ __forceinline__ void dft8(cpx<T>* u) {
+  const T r2 = T(0.70710678118654752440084436210485);
+  // stage 1: radix-2 over (j, j+4)
+  cpx<T> a0 = cadd(u[0], u[4]), a4 = csub(u[0], u[4]);
+  cpx<T> a1 = cadd(u[1], u[5]), a5 = csub(u[1], u[5]);
+  cpx<T> a2 = cadd(u[2], u[6]), a6 = csub(u[2], u[6]);
+  cpx<T> a3 = cadd(u[3], u[7]), a7 = csub(u[3], u[7]);
+  // twiddles w8^j on the odd half: a5 *= w8, a6 *= -i, a7 *= w8^3
+  a5 = {r2 * (a5.re + a5.im), r2 * (a5.im - a5.re)};
+  a6 = cmi(a6);
+  a7 = {r2 * (a7.im - a7.re), -r2 * (a7.re + a7.im)};
+  cpx<T> e[4] = {a0, a1, a2, a3}, o[4] = {a4, a5, a6, a7};
+  dft4(e);
+  dft4(o);
+  u[0] = e[0]; u[2] = e[1]; u[4] = e[2]; u[6] = e[3];
+  u[1] = o[0]; u[3] = o[1]; u[5] = o[2]; u[7] = o[3];
+}
+
+// Reordering of Makhoul's DCT via FFT: position r of the FFT sequence holds
+// element 2r (r < K/2) or element 2(K-1-r)+1 (r >= K/2).
+__device__ __forceinline__ int makhoul_perm(int r, int K) {
+  return r < (K >> 1) ? 2 * r : 2 * (K - 1 - r) + 1;
+}
+
+// One radix-R pass of the Stockham FFT (in place, register staged: every
+// thread reads its values, the block synchronises, then every thread writes
+// its results).  Butterfly i (0 <= i < K/R) reads elements i + r K/R,
+// twiddles them by exp(-2 pi i r (i mod prod) / (prod R)), applies the
+// R-point DFT and writes element (i - i mod prod) R + (i mod prod) + r prod.
+// Sequence elements are Q complex values apart.
+template <typename T, int R>
+__device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassParams& P, int Q, int tau,
+                                         int tps, int prod, bool perm_in, bool perm_out) {
+  const int K = P.ax.K;
+  const int T_ = K / R;
+  const int nb = P.V / R;
+  constexpr int GMAX = kMaxV / R;
+  cpx<T> u[GMAX * R];
+  if (active) {
+#pragma unroll
+    for (int g = 0; g < GMAX; ++g) {
+      if (g < nb) {
+        const int i = tau + g * tps;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          int idx = i + r * T_;
+          int src = perm_in ? makhoul_perm(idx, K) : idx;
+          u[g * R + r] = base[src * Q];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const int stride = K / (prod * R);
+#pragma unroll
+    for (int g = 0; g < GMAX; ++g) {
+      if (g < nb) {
+        const int i = tau + g * tps;
+        const int kk = i % prod;
+        if (prod > 1) {
+#pragma unroll
+          for (int r = 1; r < R; ++r) u[g * R + r] = cmul(u[g * R + r], ld_cpx<T>(P.ax.tw, r * kk * stride));
+        }
+        if (R == 2) dft2(&u[g * R]);
+        if (R == 3) dft3(&u[g * R]);
+        if (R == 4) dft4(&u[g * R]);
+        if (R == 8) dft8(&u[g * R]);
+        const int j = (i - kk) * R + kk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          int dst = j + r * prod;
+          if (perm_out) dst = makhoul_perm(dst, K);
+          base[dst * Q] = u[g * R + r];
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Mixed-radix Stockham FFT over nseq complex sequences of length K; sequence
+// s = (pencil, q) lives at sm + pencil * pitch + q with stride Q.
+// perm_in: the first pass reads element makhoul_perm(idx) (DCT-II input
+// reordering); perm_out: the last pass writes element makhoul_perm(idx)
+// (DCT-III output reordering).
+template <typename T>
+__device__ void fft_all(cpx<T>* sm, const PassParams& P, int nseq, int Q, bool perm_in, bool perm_out) {
+  const int K = P.ax.K;
+  const int tps = K / P.V;                  // tasks per sequence
+  const int spr = blockDim.x / tps;         // sequences per round (host: >= 1)
+  const int seq_local = threadIdx.x / tps;
+  const int tau = threadIdx.x - seq_local * tps;
+  for (int s0 = 0; s0 < nseq; s0 += spr) {
+    const int seq = s0 + seq_local;
+    const bool active = (seq_local < spr) && (seq < nseq);
+    cpx<T>* base = sm;
+    if (active) {
+      int pen = seq / Q, q = seq - pen * Q;
+      base = sm + pen * P.pitch + q;
+    }
+    int prod = 1;
+    for (int ps = 0; ps < P.npass; ++ps) {
+      const int R = P.radix[ps];
+      const bool pin = perm_in && ps == 0, pout = perm_out && ps == P.npass - 1;
+      if (R == 8) fft_pass<T, 8>(base, active, P, Q, tau, tps, prod, pin, pout);
+      else if (R == 4) fft_pass<T, 4>(base, active, P, Q, tau, tps, prod, pin, pout);
+      else if (R == 3) fft_pass<T, 3>(base, active, P, Q, tau, tps, prod, pin, pout);
+      else fft_pass<T, 2>(base, active, P, Q, tau, tps, prod, pin, pout);
+      prod *= R;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T load_in(const PassParams& P, size_t off) {
+  if (P.in_f64) return T(reinterpret_cast<const double*>(P.in)[off]);
+  return T(reinterpret_cast<const float*>(P.in)[off]);
+}
+template <typename T>
+__device__ __forceinline__ void store_out(const PassParams& P, size_t off, T v) {
+  if (P.out_f64) {
+    double* o = reinterpret_cast<double*>(P.out);
+    o[off] = P.accum ? o[off] + double(v) : double(v);
+  } else {
+    float* o = reinterpret_cast<float*>(P.out);
+    o[off] = P.accum ? o[off] + float(v) : float(v);
+  }
+}
+
+// global offset of pencil p, element i of this CTA's tile, or -1 if absent
+__device__ __forceinline__ long long pencil_offset(const PassGeom& g, int p, int i) {
+  const long long tile = blockIdx.x;
+  if (g.inner == 1) {
+    long long o = tile * g.W + p;
+    if (o >= g.outer) return -1;
+    return o * g.M + i;
+  }
+  long long o = tile / g.tiles_inner;
+  long long w = (tile - o * g.tiles_inner) * g.W + p;
+  if (w >= g.inner) return -1;
+  return (o * g.M + i) * g.inner + w;
+}
+
+// fine index j (or spectral sigma+1) -> real offset within a pencil
+template <int NORD, int Q2>
+__device__ __forceinline__ int chunk_slot(int j) {
+  int e = j / NORD;
+  return e * Q2 + (j - e * NORD);
+}
+
+template <typename T, int NORD>
+__device__ void load_tile(T* smr, const PassParams& P, bool spectral) {
+  constexpr int Q = NORD / 2 + 1;
+  const PassGeom& g = P.g;
+  const int total = g.W * g.M;
+  for (int f = threadIdx.x; f < total; f += blockDim.x) {
+    int p, i;
+    if (g.inner == 1) { p = f / g.M; i = f - p * g.M; }
+    else { i = f / g.W; p = f - i * g.W; }
+    long long off = pencil_offset(g, p, i);
+    T v = off >= 0 ? load_in<T>(P, (size_t)off) : T(0);
+    smr[2 * p * P.pitch + chunk_slot<NORD, 2 * Q>(spectral ? i + 1 : i)] = v;
+  }
+}
+
+template <typename T, int NORD>
+__device__ void store_tile(const T* smr, const PassParams& P, bool spectral) {
+  constexpr int Q = NORD / 2 + 1;
+  const PassGeom& g = P.g;
+  const int total = g.W * g.M;
+  for (int f = threadIdx.x; f < total; f += blockDim.x) {
+    int p, i;
+    if (g.inner == 1) { p = f / g.M; i = f - p * g.M; }
+    else { i = f / g.W; p = f - i * g.W; }
+    long long off = pencil_offset(g, p, i);
+    if (off >= 0) store_out<T>(P, (size_t)off, smr[2 * p * P.pitch + chunk_slot<NORD, 2 * Q>(spectral ? i + 1 : i)]);
+  }
+}
+
+// Build the Q packed complex sequences of every pencil in place:
+// q = 0: (node sum, node difference); q = m: (y[m] + y[n-m], y[m] - y[n-m]);
+// the sine (real) parts modulated by (-1)^e (DST-II via DCT-II).
+template <typename T, int NORD>
+__device__ void build_sequences(cpx<T>* sm, const PassParams& P) {
+  constexpr int Q = NORD / 2 + 1;
+  const int K = P.ax.K;
+  const int nchunks = P.g.W * K;
+  T xl[kMaxChunkTasks];
+#pragma unroll
+  for (int t = 0; t < kMaxChunkTasks; ++t) {
+    int c = threadIdx.x + t * blockDim.x;
+    xl[t] = T(0);
+    if (c < nchunks) {
+      int p = c / K, e = c - p * K;
+      const T* smr = reinterpret_cast<const T*>(sm + p * P.pitch);
+      if (e > 0) xl[t] = smr[(e - 1) * 2 * Q + (NORD - 1)];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < kMaxChunkTasks; ++t) {
+    int c = threadIdx.x + t * blockDim.x;
+    if (c < nchunks) {
+      int p = c / K, e = c - p * K;
+      T* smr = reinterpret_cast<T*>(sm + p * P.pitch) + e * 2 * Q;
+      T y[NORD];
+#pragma unroll
+      for (int s = 0; s < NORD; ++s) y[s] = smr[s];
+      T xr = (e < K - 1) ? y[NORD - 1] : T(0);
+      T sg = (e & 1) ? T(-1) : T(1);
+      cpx<T> out[Q];
+      out[0] = {sg * (xr + xl[t]), xr - xl[t]};
+#pragma unroll
+      for (int q = 1; q < Q; ++q) {
+        if (2 * q < NORD) out[q] = {sg * (y[q - 1] + y[NORD - q - 1]), y[q - 1] - y[NORD - q - 1]};
+        else out[q] = {sg * y[q - 1], T(0)};
+      }
+      cpx<T>* dst = reinterpret_cast<cpx<T>*>(smr);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) dst[q] = out[q];
+    }
+  }
+  __syncthreads();
+}
+
+// Reconstruct the fine-grid values of every element from the DCT-III outputs
+// x_e[q] (sine part (-1)^e Re, cosine part Im), in place.
+template <typename T, int NORD>
+__device__ void reconstruct(cpx<T>* sm, const PassParams& P) {
+  constexpr int Q = NORD / 2 + 1;
+  const int K = P.ax.K;
+  const int nchunks = P.g.W * K;
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
+    int p = c / K, e = c - p * K;
+    cpx<T>* ch = sm + p * P.pitch + e * Q;
+    cpx<T> x[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) x[q] = ch[q];
+    T sg = (e & 1) ? T(-1) : T(1);
+    T* smr = reinterpret_cast<T*>(ch);
+    smr[NORD - 1] = sg * x[0].re + x[0].im;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+      T ys = sg * x[q].re, yc = x[q].im;
+      if (2 * q < NORD) {
+        smr[q - 1] = ys + yc;
+        smr[NORD - q - 1] = ys - yc;
+      } else {
+        smr[q - 1] = ys;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int NORD>
+__device__ __forceinline__ T pencil_den_base(const PassParams& P, int p) {
+  // c + sum over the other axes of a_j mu_j[sigma_j] for the pencil p of this
+  // CTA (fused pass on axis 0: the pencil index is the flat index of the
+  // later axes).
+  const PassGeom& g = P.g;
+  long long w = 0;    // inner == 1: the later axes (if any) all have size 1
+  if (g.inner > 1) {
+    long long tile = blockIdx.x;
+    long long o = tile / g.tiles_inner;
+    w = (tile - o * g.tiles_inner) * g.W + p;
+    if (w >= g.inner) w = 0;
+  }
+  double base = P.dv.c;
+  if (P.dv.nother == 1) {
+    base += double(reinterpret_cast<const T*>(P.dv.mu_o[0])[w]);
+  } else if (P.dv.nother == 2) {
+    long long i1 = w / P.dv.Mo[1], i2 = w - i1 * P.dv.Mo[1];
+    base += double(reinterpret_cast<const T*>(P.dv.mu_o[0])[i1]);
+    base += double(reinterpret_cast<const T*>(P.dv.mu_o[1])[i2]);
+  }
+  return T(base);
+}
+
+// Per frequency pair (k, K-k): forward post-twiddle and n x (n+1) maps
+// (MODE_FWD: write spectral coefficients), optionally the divide and the
+// inverse maps and pre-twiddle (MODE_FUSED); MODE_INV starts from spectral
+// coefficients in shared memory.
+template <typename T, int NORD, int MODE>
+__device__ void spectral_stage(cpx<T>* sm, const PassParams& P) {
+  constexpr int Q = NORD / 2 + 1;
+  constexpr int QC = (NORD - 1) / 2 + 1;
+  constexpr int N1 = NORD + 1;
+  const int K = P.ax.K;
+  const int npairs = K / 2 + 1;
+  const T* F = reinterpret_cast<const T*>(P.ax.fwd);
+  const T* I = reinterpret_cast<const T*>(P.ax.inv);
+  const T* mu = reinterpret_cast<const T*>(P.ax.mu);
+  const int ntask = P.g.W * npairs;
+  for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+    const int p = task / npairs;
+    const int k = task - p * npairs;
+    cpx<T>* pen = sm + p * P.pitch;
+    T* penr = reinterpret_cast<T*>(pen);
+    T wk[NORD], wkk[NORD];       // spectral values of k and K-k
+    const int kk = (k == 0) ? 0 : K - k;
+    if (MODE == MODE_FWD || MODE == MODE_FUSED) {
+      if (k == 0) {
+        T in[N1];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) in[q - 1] = pen[q].re;          // S_m(K)
+#pragma unroll
+        for (int q = 1; q < QC; ++q) in[Q - 1 + q - 1] = pen[q].im; // C_m(0)
+#pragma unroll
+        for (int l = 0; l < NORD - 1; ++l) {
+          T acc = T(0);
+#pragma unroll
+          for (int j = 0; j < NORD - 1; ++j) acc += __ldg(&F[l * N1 + j]) * in[j];
+          wk[l] = acc;
+        }
+      } else {
+        cpx<T> rk = ld_cpx<T>(P.ax.rot, k);     // exp(-i phi_k)
+        cpx<T> rkc = {rk.re, -rk.im};
+        T ink[N1], inkk[N1];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          cpx<T> A = cmul(rk, pen[k * Q + q]);
+          cpx<T> B = cmul(rkc, pen[kk * Q + q]);
+          ink[q] = B.im - A.im;                 // 2 S(k)
+          inkk[q] = A.re + B.re;                // 2 S(K-k)
+          if (q < QC) {
+            ink[Q + q] = A.im + B.im;           // 2 C(k)
+            inkk[Q + q] = A.re - B.re;          // 2 C(K-k)
+          }
+        }
+        const T* Fk = F + (size_t)k * NORD * N1;
+        const T* Fkk = F + (size_t)kk * NORD * N1;
+#pragma unroll
+        for (int l = 0; l < NORD; ++l) {
+          T a = T(0), b = T(0);
+#pragma unroll
+          for (int j = 0; j < N1; ++j) {
+            a += __ldg(&Fk[l * N1 + j]) * ink[j];
+            b += __ldg(&Fkk[l * N1 + j]) * inkk[j];
+          }
+          wk[l] = a;
+          wkk[l] = b;
+        }
+      }
+    } else {   // MODE_INV: read spectral values
+      if (k == 0) {
+#pragma unroll
+        for (int l = 0; l < NORD - 1; ++l) wk[l] = penr[1 + l];
+      } else {
+#pragma unroll
+        for (int l = 0; l < NORD; ++l) {
+          wk[l] = penr[k * 2 * Q + l];
+          wkk[l] = penr[kk * 2 * Q + l];
+        }
+      }
+    }
+    if (MODE == MODE_FWD) {
+      if (k == 0) {
+#pragma unroll
+        for (int l = 0; l < NORD - 1; ++l) penr[1 + l] = wk[l];
+      } else {
+#pragma unroll
+        for (int l = 0; l < NORD; ++l) {
+          penr[k * 2 * Q + l] = wk[l];
+          if (kk != k) penr[kk * 2 * Q + l] = wkk[l];
+        }
+      }
+      continue;
+    }
+    if (MODE == MODE_FUSED) {
+      T base = pencil_den_base<T, NORD>(P, p);
+      if (k == 0) {
+#pragma unroll
+        for (int l = 0; l < NORD - 1; ++l) wk[l] = wk[l] / (base + __ldg(&mu[l]));
+      } else {
+#pragma unroll
+        for (int l = 0; l < NORD; ++l) {
+          wk[l] = wk[l] / (base + __ldg(&mu[NORD * k - 1 + l]));
+          wkk[l] = wkk[l] / (base + __ldg(&mu[NORD * kk - 1 + l]));
+        }
+      }
+    }
+    // inverse maps and pre-twiddle
+    if (k == 0) {
+      // H_0 = a(K) + i b(0): bubble parts only (node coefficients vanish)
+      cpx<T> H[Q];
+      H[0] = {T(0), T(0)};
+#pragma unroll
+      for (int q = 1; q < Q; ++q) {
+        T a = T(0), b = T(0);
+#pragma unroll
+        for (int l = 0; l < NORD - 1; ++l) {
+          a += __ldg(&I[(q - 1) * NORD + l]) * wk[l];
+          if (q < QC) b += __ldg(&I[(Q - 1 + q - 1) * NORD + l]) * wk[l];
+        }
+        H[q] = {a, b};
+      }
+#pragma unroll
+      for (int q = 0; q < Q; ++q) pen[q] = H[q];
+    } else {
+      const T* Ik = I + (size_t)k * N1 * NORD;
+      const T* Ikk = I + (size_t)kk * N1 * NORD;
+      T ak[N1], akk[N1];
+#pragma unroll
+      for (int j = 0; j < N1; ++j) {
+        T a = T(0), b = T(0);
+#pragma unroll
+        for (int l = 0; l < NORD; ++l) {
+          a += __ldg(&Ik[j * NORD + l]) * wk[l];
+          b += __ldg(&Ikk[j * NORD + l]) * wkk[l];
+        }
+        ak[j] = a;
+        akk[j] = b;
+      }
+      cpx<T> rk = ld_cpx<T>(P.ax.rot, k);       // exp(-i phi_k)
+      // exp(-i phi_{K-k}) = -i exp(+i phi_k)
+      cpx<T> rkk = cmi(cpx<T>{rk.re, -rk.im});
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        T bk = (q < QC) ? ak[Q + q] : T(0);
+        T bkk = (q < QC) ? akk[Q + q] : T(0);
+        cpx<T> Hk = cmul(rk, cpx<T>{akk[q] - bkk, ak[q] + bk});
+        pen[k * Q + q] = Hk;
+        if (kk != k) {
+          cpx<T> Hkk = cmul(rkk, cpx<T>{ak[q] - bk, akk[q] + bkk});
+          pen[kk * Q + q] = Hkk;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int NORD, int MODE>
+__global__ void __launch_bounds__(kPencilThreads, 1) pencil_pass_kernel(PassParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
+  T* smr = reinterpret_cast<T*>(smem_raw);
+  constexpr int Q = NORD / 2 + 1;
+  if (MODE == MODE_INV) {
+    load_tile<T, NORD>(smr, P, true);
+    __syncthreads();
+    spectral_stage<T, NORD, MODE_INV>(sm, P);
+    fft_all<T>(sm, P, P.g.W * Q, Q, false, true);
+    reconstruct<T, NORD>(sm, P);
+    store_tile<T, NORD>(smr, P, false);
+  } else {
+    load_tile<T, NORD>(smr, P, false);
+    __syncthreads();
+    build_sequences<T, NORD>(sm, P);
+    fft_all<T>(sm, P, P.g.W * Q, Q, true, false);
+    spectral_stage<T, NORD, MODE>(sm, P);
+    if (MODE == MODE_FWD) {
+      store_tile<T, NORD>(smr, P, true);
+    } else {
+      fft_all<T>(sm, P, P.g.W * Q, Q, false, true);
+      reconstruct<T, NORD>(sm, P);
+      store_tile<T, NORD>(smr, P, false);
+    }
+  }
+}
+
+}  // namespace femfft

@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (relative L2 over all DOF and right-hand sides): 1e-12 for the
+FP64 path and 1e-10 for the mixed path after refinement (the solver's
+accuracy targets); transforms and the operator apply are checked at 1e-12 /
+1e-13."""
+
+import numpy as np
+import pytest
+
+from oracle import fem1d, harness, solve as osolve
+from paper_1701_03967_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _plan(case, precision="fp64", max_nrhs=1):
+    from paper_1701_03967_gb300 import Plan
+    return Plan(case["n"], case["K"], case.get("X"), case.get("a"), case.get("c", 0.0), precision,
+                max_nrhs=max_nrhs)
+
+
+def _prob(case):
+    return osolve.Problem(case["n"], case["K"], case.get("X"), case.get("a"), case.get("c", 0.0))
+
+
+def _rel(x, y):
+    return float(np.linalg.norm(x - y) / np.linalg.norm(y))
+
+
+CASES = [
+    dict(n=3, K=(8,), X=(1.3,), a=(0.7,), c=0.2),
+    dict(n=9, K=(16,), c=1.0),
+    dict(n=1, K=(2,)),
+    dict(n=2, K=(6,), X=(2.0,), a=(1.5,), c=-1.0),
+    dict(n=5, K=(48,)),
+    dict(n=2, K=(16, 16)),
+    dict(n=9, K=(16, 32), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
+    dict(n=4, K=(12, 8), X=(0.7, 1.1), a=(2.0, 0.5), c=0.3),
+    dict(n=7, K=(6, 4)),
+    dict(n=1, K=(64, 2), c=3.0),
+    dict(n=8, K=(32, 16), a=(3.0, 1.0)),
+    dict(n=6, K=(24, 18)),
+    dict(n=3, K=(4, 8, 6), X=(1.0, 1.5, 0.5), a=(1.0, 0.6, 2.0), c=0.1),
+    dict(n=9, K=(4, 4, 4)),
+    dict(n=2, K=(16, 8, 12), c=2.0),
+    dict(n=5, K=(8, 8, 8)),
+    dict(n=4, K=(2, 2, 2)),
+]
+
+
+def _ids(c):
+    return f"n{c['n']}_K{'x'.join(map(str, c['K']))}"
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_solve_fp64_matches_oracle(case):
+    prob = _prob(case)
+    b = synth.normal_batch(2, prob.M, synth.CFG_TEST, 101)
+    want = osolve.solve(prob, b)
+    plan = _plan(case, "fp64", max_nrhs=2)
+    got = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_solve_mixed_matches_oracle(case):
+    prob = _prob(case)
+    b = synth.normal_batch(2, prob.M, synth.CFG_TEST, 102)
+    want = osolve.solve(prob, b)
+    plan = _plan(case, "mixed", max_nrhs=2)
+    plan.set_refinement(0.0, 2)
+    got = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(got, want) <= 1e-10
+
+
+@pytest.mark.parametrize("case", CASES[::2], ids=_ids)
+def test_apply_matches_oracle(case):
+    prob = _prob(case)
+    u = synth.normal_batch(2, prob.M, synth.CFG_TEST, 103)
+    want = osolve.apply(prob, u)
+    plan = _plan(case, "fp64", max_nrhs=2)
+    got = plan.apply(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert _rel(got, want) <= 1e-13
+
+
+def _bubble_signs(plan, prob):
+    """Per-axis sign vectors aligning the library's bubble eigenvectors e^(l)
+    (sign is free) with the oracle's."""
+    signs = []
+    for i in range(prob.N):
+        lam, cn, p = plan.axis_tables(i)
+        _, S, _ = prob.basis1d(i)
+        sg = np.ones(prob.M[i])
+        n = prob.n
+        for l in range(n - 1):
+            sg[l] = np.sign(p[0, l] @ S[0:n - 1, l])
+        signs.append(sg)
+    return signs
+
+
+@pytest.mark.parametrize("case", CASES[::3], ids=_ids)
+def test_forward_and_inverse_transforms_match_oracle(case):
+    prob = _prob(case)
+    y = synth.normal_field(prob.M, synth.CFG_TEST, 104)
+    plan = _plan(case, "fp64")
+    got = plan.forward(torch.from_numpy(y).cuda()).cpu().numpy()
+    want = osolve.forward_coefficients(prob, y)
+    sg = _bubble_signs(plan, prob)
+    S = np.ones(prob.M)
+    for i, s in enumerate(sg):
+        shape = [1] * prob.N
+        shape[i] = prob.M[i]
+        S = S * s.reshape(shape)
+    assert _rel(got * S, want) <= 1e-12
+    w = synth.normal_field(prob.M, synth.CFG_TEST, 105)
+    got_w = plan.inverse(torch.from_numpy(w * S).cuda()).cpu().numpy()
+    assert _rel(got_w, osolve.inverse_expansion(prob, w)) <= 1e-12
+
+
+def test_manufactured_solution_error_matches_paper_table():
+    """2D, n=5, K=16: max-norm error 5.4e-8 (Section 5 table, algorithm (a))."""
+    u, f = harness.manufactured(harness.PAPER_2D, 2, (1, 1), 1.0)
+    case = dict(n=5, K=(16, 16), c=1.0)
+    prob = _prob(case)
+    b = np.ascontiguousarray(harness.load_vector(prob, f))
+    plan = _plan(case, "fp64")
+    uh = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
+    err = harness.max_error(prob, uh, u)
+    assert abs(err / 5.4e-8 - 1) < 0.06
+
+
+def test_edge_cases():
+    from paper_1701_03967_gb300 import FemFftError, Plan
+    case = dict(n=3, K=(8, 4))
+    prob = _prob(case)
+    plan = _plan(case, "fp64", max_nrhs=2)
+    # nrhs larger than the workspace: processed in groups
+    b = synth.normal_batch(5, prob.M, synth.CFG_TEST, 106)
+    got = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(got, osolve.solve(prob, b)) <= 1e-12
+    # in-place FP64 solve
+    bt = torch.from_numpy(b[:2].copy()).cuda()
+    plan.solve(bt, out=bt)
+    assert _rel(bt.cpu().numpy(), osolve.solve(prob, b[:2])) <= 1e-12
+    # zero right-hand sides
+    z = torch.zeros((0,) + prob.M, dtype=torch.float64, device="cuda")
+    plan.solve(z)
+    # zero input gives zero output
+    assert float(plan.solve(torch.zeros(prob.M, dtype=torch.float64, device="cuda")).abs().max()) == 0.0
+    # invalid arguments
+    for bad in [dict(n=3, K=(7, 4)), dict(n=0, K=(8,)), dict(n=10, K=(8,)), dict(n=3, K=(8,), c=-100.0),
+                dict(n=3, K=(8,), a=(-1.0,)), dict(n=2, K=(4, 4, 4, 4))]:
+        with pytest.raises(FemFftError):
+            Plan(bad["n"], bad["K"], None, bad.get("a"), bad.get("c", 0.0))
+    mixed = _plan(case, "mixed")
+    with pytest.raises(FemFftError):
+        mixed.solve(bt[0], out=bt[0])
+    with pytest.raises(TypeError):
+        plan.solve(torch.zeros(prob.M, dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("case", [dict(n=2, K=(4, 6), a=(1.2, 0.7), c=0.5), dict(n=3, K=(4, 2, 4), c=0.3)],
+                         ids=_ids)
+def test_grad_coeffs_match_oracle(case):
+    prob = _prob(case)
+    f = synth.normal_batch(2, prob.M, synth.CFG_TEST, 107)
+    ut = synth.normal_batch(2, prob.M, synth.CFG_TEST, 108)
+    u = osolve.solve(prob, f)
+    gf, ga, gc = osolve.grad(prob, f, 2 * (u - ut))
+    plan = _plan(case, "fp64", max_nrhs=2)
+    ud = plan.solve(torch.from_numpy(f).cuda())
+    lam = plan.solve(2 * (ud - torch.from_numpy(ut).cuda()))
+    ga_g, gc_g = plan.grad_coeffs(ud, lam)
+    np.testing.assert_allclose(ga_g, ga, rtol=1e-10)
+    np.testing.assert_allclose(gc_g, gc, rtol=1e-10)
+    assert _rel(lam.cpu().numpy(), gf) <= 1e-12

@@ -1,0 +1,69 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol,
+and its host-side plan precompute (double-double eigenpairs, Section 3,
+Theorem 1) agrees with the oracle.  No device call is made."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import fem1d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    from paper_1701_03967_gb300 import _lib as L
+    if not os.path.exists(L.LIB_PATH):
+        from paper_1701_03967_gb300 import build
+        build.build()
+    return L.lib()
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib()
+    header = open(os.path.join(ROOT, "include", "femfft.h")).read()
+    names = set(re.findall(r"^\s*(?:int|const char\*)\s+(fem_fft_\w+)\s*\(", header, re.M))
+    assert len(names) >= 14
+    for name in sorted(names):
+        assert hasattr(L, name), name
+
+
+def _precompute(n, K, X=1.0):
+    L = _lib()
+    M = max(n * K - 1, 1)
+    lam, cn = np.zeros(M), np.zeros(M)
+    p = np.zeros(max(K, 1) * max(n, 1) * max(n - 1, 1))
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = L.fem_fft_axis_precompute(n, K, X, lam.ctypes.data_as(dp), cn.ctypes.data_as(dp), p.ctypes.data_as(dp))
+    return rc, lam, cn, p.reshape(max(K, 1), max(n, 1), max(n - 1, 1))
+
+
+@pytest.mark.parametrize("n,K", [(1, 8), (2, 6), (3, 16), (4, 12), (5, 8), (6, 4), (7, 8), (8, 6), (9, 16), (9, 2)])
+def test_host_eigenpairs_match_oracle(n, K):
+    rc, lam, cn, p = _precompute(n, K)
+    assert rc == 0
+    lo, S, co = fem1d.theorem1_basis(n, K)
+    np.testing.assert_allclose(lam, lo, rtol=1e-14)
+    np.testing.assert_allclose(cn, co, rtol=1e-13)
+    # p_k^(l): interiors of element 1 of s_k^(l) are flip(p) sin(pi k / K)
+    for k in range(1, K):
+        for l in range(n):
+            col = n - 1 + (k - 1) * n + l
+            if n > 1:
+                want = fem1d.flip(S[0:n - 1, col]) / np.sin(np.pi * k / K)
+                np.testing.assert_allclose(p[k, l], want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
+    # bubble eigenvectors e^(l) up to sign
+    for l in range(n - 1):
+        e_or = S[0:n - 1, l]
+        e = p[0, l]
+        sgn = np.sign(e @ e_or)
+        np.testing.assert_allclose(sgn * e, e_or, atol=1e-13)
+
+
+def test_host_rejects_bad_sizes():
+    for n, K in [(0, 8), (10, 8), (3, 5), (3, 1), (3, 10), (3, 7)]:
+        rc, *_ = _precompute(n, K)
+        assert rc == -1, (n, K)
