@@ -216,7 +216,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
-    ap.add_argument("--refine", type=int, default=1, help="refinement steps of the mixed path")
+    ap.add_argument("--refine", type=int, default=2, help="refinement steps of the mixed path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]

@@ -103,7 +103,7 @@ int fem_fft_plan_destroy(fem_fft_plan plan);
  *             FP64 precision, and in MIXED precision only with refinement
  *             disabled (max_iter = 0), else FEM_FFT_ERR_ARG.
  * FP64: 2N-1 pencil passes in float64.  MIXED: the passes in float32, then
- * max_iter (default 1) refinement steps r = b - L u (float64, matrix-free),
+ * max_iter (default 2) refinement steps r = b - L u (float64, matrix-free),
  * u += L^{-1} r (float32 passes), stopping early when the relative residual
  * ||r||_2 / ||b||_2 <= rtol (default 0: always take max_iter steps).  The
  * residual norms are read back at the end of each step only when rtol > 0.

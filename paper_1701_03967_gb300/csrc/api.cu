@@ -90,11 +90,12 @@ struct fem_fft_plan_s {
   AxisHost ax[kMaxN];
   DevTables t64[kMaxN], t32[kMaxN];
   std::vector<double> Aref, Cref;      // element matrices
+  std::vector<double> Crow;            // exact row sums of Cref (those of Aref are 0)
   float* w32 = nullptr;                // mixed workspace [max_nrhs][dof]
   double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};   // float64 temporaries
   double* d_scalars = nullptr;         // device scalars (norms, dots)
   double rtol = 0.0;
-  int max_iter = 1;
+  int max_iter = 2;
   int last_iters = -1;
   double last_rel = -1.0;
   int smem_optin = 0;
@@ -200,11 +201,12 @@ int plan_pass(fem_fft_plan p, int axis, long long outer, long long inner, bool f
   const size_t per_pen = (size_t)pitch * csize;
   const size_t budget = (size_t)std::min(p->smem_optin, 220 * 1024);
   long long wmax = (long long)(budget / per_pen);
+  wmax = std::min<long long>(wmax, f64 ? kMaxW64 : kMaxW);
   if (wmax < 1) {
     g_last_error = "pencil does not fit in shared memory";
     return FEM_FFT_ERR_ARG;
   }
-  const int threads = kPencilThreads;
+  const int threads = f64 ? kPencilThreads64 : kPencilThreads;
   // chunk tasks of the sequence build: W * K <= kMaxChunkTasks * threads
   wmax = std::min<long long>(wmax, (long long)kMaxChunkTasks * threads / K);
   if (wmax < 1 || K / P.V > threads) {
@@ -326,6 +328,7 @@ int apply_launch(fem_fft_plan p, const ApplyParams& P, cudaStream_t s) {
   } else {
     for (int j = 0; j < P.nout; ++j) bytes += elems * ((j == 0 && P.out0_f32) ? 4.0 : 8.0);
     if (P.base) bytes += elems * 8.0;
+    if (P.addend) bytes += elems * 8.0;
   }
   const double n1 = P.n + 1;
   const double flops = elems * P.nterm * 2.0 * n1 * n1 / P.n;
@@ -333,9 +336,18 @@ int apply_launch(fem_fft_plan p, const ApplyParams& P, cudaStream_t s) {
   return launch_apply(P, s);
 }
 
+// Term t of an apply launch: matrix alpha E + beta E2 where E, E2 are the
+// plan's stiffness (Aref) or mass (Cref) element matrices; its exact row sums
+// are alpha (E 1) + beta (E2 1) with A 1 = 0 and C 1 = Crow.
 void set_mat(ApplyParams& A, int t, const std::vector<double>& E, double alpha, const std::vector<double>* E2,
-             double beta, int n1) {
+             double beta, int n1, const std::vector<double>& Aref, const std::vector<double>& Crow) {
   for (int i = 0; i < n1 * n1; ++i) A.mats[t][i] = alpha * E[i] + (E2 ? beta * (*E2)[i] : 0.0);
+  const bool e_is_mass = &E != &Aref;
+  for (int r = 0; r < n1; ++r) {
+    double v = e_is_mass ? alpha * Crow[r] : 0.0;
+    if (E2 && E2 != &Aref) v += beta * Crow[r];
+    A.rows1[t][r] = v;
+  }
 }
 
 ApplyParams apply_base(fem_fft_plan p, int axis, long long nrhs) {
@@ -353,7 +365,12 @@ ApplyParams apply_base(fem_fft_plan p, int axis, long long nrhs) {
 }
 
 // kind 0: out = L u (float64);  kind 1: r = b - L u (float32 into r32, norms
-// optional);  the temporaries p->tmp hold the partial products.
+// optional).  Every stiffness factor acts on u directly and the mass factors
+// are applied to its result (see apply.cu for why):
+//   1D: L u = E_1 u,  E_1 = a_1 s_1 A + c C
+//   2D: L u = C_2 (E_1 u) + C_1 (a_2 s_2 A_2 u)
+//   3D: L u = C_3 [C_2 (E_1 u) + C_1 (a_2 s_2 A_2 u)] + C_1 C_2 (a_3 s_3 A_3 u)
+// The temporaries p->tmp hold the partial products.
 int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, double* out, const double* b,
                    float* r32, double* norms, cudaStream_t s) {
   const int N = p->N, n1 = p->n + 1;
@@ -370,80 +387,78 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
       P.norms = norms;
     }
   };
-  int e;
-  if (N == 1) {
-    ApplyParams P = apply_base(p, 0, nrhs);
-    P.in[0] = u;
+  auto one = [&](int axis, const double* in, double* o, const std::vector<double>& E, double alpha,
+                 const std::vector<double>* E2, double beta) {
+    ApplyParams P = apply_base(p, axis, nrhs);
+    P.in[0] = in;
     P.nterm = 1;
     P.nout = 1;
-    set_mat(P, 0, A, s_[0], &C, p->c, n1);
+    P.out[0] = o;
+    set_mat(P, 0, E, alpha, E2, beta, n1, p->Aref, p->Crow);
+    return P;
+  };
+  int e;
+  if (N == 1) {
+    ApplyParams P = one(0, u, nullptr, A, s_[0], &C, p->c);
     finish(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
     return FEM_FFT_OK;
   }
-  if (N == 2) {
-    ApplyParams P = apply_base(p, 1, nrhs);       // t1 = C2 u, t2 = A2 u
-    P.in[0] = u;
+  double *X = p->tmp[0], *Y = p->tmp[1], *Z = p->tmp[2], *W = p->tmp[3];
+  {
+    ApplyParams P = one(0, u, X, A, s_[0], &C, p->c);                   // X = E_1 u
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+  }
+  {
+    ApplyParams P = apply_base(p, 1, nrhs);                             // Y = C_2 X, Z = a2 s2 A_2 u
+    P.in[0] = X;
+    P.in[1] = u;
     P.nterm = 2;
     P.nout = 2;
-    P.out[0] = p->tmp[0];
-    P.out[1] = p->tmp[1];
-    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1);
+    P.out[0] = Y;
+    P.out[1] = Z;
+    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
     P.t_src[0] = 0; P.t_dst[0] = 0;
-    set_mat(P, 1, A, s_[1], nullptr, 0.0, n1);
-    P.t_src[1] = 0; P.t_dst[1] = 1;
+    set_mat(P, 1, A, s_[1], nullptr, 0.0, n1, p->Aref, p->Crow);
+    P.t_src[1] = 1; P.t_dst[1] = 1;
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
-    ApplyParams Q = apply_base(p, 0, nrhs);       // (a1 s1 A1 + c C1) t1 + C1 t2
-    Q.in[0] = p->tmp[0];
-    Q.in[1] = p->tmp[1];
-    Q.nterm = 2;
-    Q.nout = 1;
-    set_mat(Q, 0, A, s_[0], &C, p->c, n1);
-    Q.t_src[0] = 0; Q.t_dst[0] = 0;
-    set_mat(Q, 1, C, 1.0, nullptr, 0.0, n1);
-    Q.t_src[1] = 1; Q.t_dst[1] = 0;
-    finish(Q);
-    if ((e = apply_launch(p, Q, s))) return cuda_fail((cudaError_t)e, "apply");
+  }
+  if (N == 2) {
+    ApplyParams P = one(0, Z, nullptr, C, 1.0, nullptr, 0.0);          // L u = Y + C_1 Z
+    P.addend = Y;
+    finish(P);
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
     return FEM_FFT_OK;
   }
-  // N == 3: t = C3 u, v = A3 u; w1 = C2 t, w2 = a2 s2 A2 t + a3 s3 C2 v;
-  // L u = (a1 s1 A1 + c C1) w1 + C1 w2
-  ApplyParams P = apply_base(p, 2, nrhs);
-  P.in[0] = u;
-  P.nterm = 2;
-  P.nout = 2;
-  P.out[0] = p->tmp[0];
-  P.out[1] = p->tmp[1];
-  set_mat(P, 0, C, 1.0, nullptr, 0.0, n1);
-  P.t_src[0] = 0; P.t_dst[0] = 0;
-  set_mat(P, 1, A, 1.0, nullptr, 0.0, n1);
-  P.t_src[1] = 0; P.t_dst[1] = 1;
-  if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
-  ApplyParams Q = apply_base(p, 1, nrhs);
-  Q.in[0] = p->tmp[0];
-  Q.in[1] = p->tmp[1];
-  Q.nterm = 3;
-  Q.nout = 2;
-  Q.out[0] = p->tmp[2];
-  Q.out[1] = p->tmp[3];
-  set_mat(Q, 0, C, 1.0, nullptr, 0.0, n1);
-  Q.t_src[0] = 0; Q.t_dst[0] = 0;
-  set_mat(Q, 1, A, s_[1], nullptr, 0.0, n1);
-  Q.t_src[1] = 0; Q.t_dst[1] = 1;
-  set_mat(Q, 2, C, s_[2], nullptr, 0.0, n1);
-  Q.t_src[2] = 1; Q.t_dst[2] = 1;
-  if ((e = apply_launch(p, Q, s))) return cuda_fail((cudaError_t)e, "apply");
-  ApplyParams R = apply_base(p, 0, nrhs);
-  R.in[0] = p->tmp[2];
-  R.in[1] = p->tmp[3];
-  R.nterm = 2;
-  R.nout = 1;
-  set_mat(R, 0, A, s_[0], &C, p->c, n1);
-  R.t_src[0] = 0; R.t_dst[0] = 0;
-  set_mat(R, 1, C, 1.0, nullptr, 0.0, n1);
-  R.t_src[1] = 1; R.t_dst[1] = 0;
-  finish(R);
-  if ((e = apply_launch(p, R, s))) return cuda_fail((cudaError_t)e, "apply");
+  {
+    ApplyParams P = one(0, Z, Y, C, 1.0, nullptr, 0.0);                 // Y += C_1 Z
+    P.addend = Y;
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+  }
+  {
+    ApplyParams P = apply_base(p, 2, nrhs);                             // W = C_3 Y, X = a3 s3 A_3 u
+    P.in[0] = Y;
+    P.in[1] = u;
+    P.nterm = 2;
+    P.nout = 2;
+    P.out[0] = W;
+    P.out[1] = X;
+    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    P.t_src[0] = 0; P.t_dst[0] = 0;
+    set_mat(P, 1, A, s_[2], nullptr, 0.0, n1, p->Aref, p->Crow);
+    P.t_src[1] = 1; P.t_dst[1] = 1;
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+  }
+  {
+    ApplyParams P = one(1, X, Z, C, 1.0, nullptr, 0.0);                 // Z = C_2 X
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+  }
+  {
+    ApplyParams P = one(0, Z, nullptr, C, 1.0, nullptr, 0.0);          // L u = W + C_1 Z
+    P.addend = W;
+    finish(P);
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+  }
   return FEM_FFT_OK;
 }
 
@@ -460,9 +475,9 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
     P.in[0] = u;
     P.nterm = 2;
     P.nout = 2;
-    set_mat(P, 0, A, s_[0], nullptr, 0.0, n1);
+    set_mat(P, 0, A, s_[0], nullptr, 0.0, n1, p->Aref, p->Crow);
     P.t_src[0] = 0; P.t_dst[0] = 0;
-    set_mat(P, 1, C, 1.0, nullptr, 0.0, n1);
+    set_mat(P, 1, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
     P.t_src[1] = 0; P.t_dst[1] = 1;
     P.dotv = lam;
     P.dots = dots;
@@ -476,9 +491,9 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
     P.nout = 2;
     P.out[0] = p->tmp[0];
     P.out[1] = p->tmp[1];
-    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1);
+    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
     P.t_src[0] = 0; P.t_dst[0] = 0;
-    set_mat(P, 1, A, 1.0, nullptr, 0.0, n1);
+    set_mat(P, 1, A, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
     P.t_src[1] = 0; P.t_dst[1] = 1;
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
     ApplyParams Q = apply_base(p, 0, nrhs);       // s1 A1 t1, s2 C1 t2, C1 t1
@@ -486,11 +501,11 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
     Q.in[1] = p->tmp[1];
     Q.nterm = 3;
     Q.nout = 3;
-    set_mat(Q, 0, A, s_[0], nullptr, 0.0, n1);
+    set_mat(Q, 0, A, s_[0], nullptr, 0.0, n1, p->Aref, p->Crow);
     Q.t_src[0] = 0; Q.t_dst[0] = 0;
-    set_mat(Q, 1, C, s_[1], nullptr, 0.0, n1);
+    set_mat(Q, 1, C, s_[1], nullptr, 0.0, n1, p->Aref, p->Crow);
     Q.t_src[1] = 1; Q.t_dst[1] = 1;
-    set_mat(Q, 2, C, 1.0, nullptr, 0.0, n1);
+    set_mat(Q, 2, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
     Q.t_src[2] = 0; Q.t_dst[2] = 2;
     Q.dotv = lam;
     Q.dots = dots;
@@ -503,9 +518,9 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
   P.nout = 2;
   P.out[0] = p->tmp[0];
   P.out[1] = p->tmp[1];
-  set_mat(P, 0, C, 1.0, nullptr, 0.0, n1);
+  set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
   P.t_src[0] = 0; P.t_dst[0] = 0;
-  set_mat(P, 1, A, 1.0, nullptr, 0.0, n1);
+  set_mat(P, 1, A, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
   P.t_src[1] = 0; P.t_dst[1] = 1;
   if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   ApplyParams Q = apply_base(p, 1, nrhs);         // w1 = C2 t, w2 = A2 t
@@ -514,9 +529,9 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
   Q.nout = 2;
   Q.out[0] = p->tmp[2];
   Q.out[1] = p->tmp[3];
-  set_mat(Q, 0, C, 1.0, nullptr, 0.0, n1);
+  set_mat(Q, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
   Q.t_src[0] = 0; Q.t_dst[0] = 0;
-  set_mat(Q, 1, A, 1.0, nullptr, 0.0, n1);
+  set_mat(Q, 1, A, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
   Q.t_src[1] = 0; Q.t_dst[1] = 1;
   if ((e = apply_launch(p, Q, s))) return cuda_fail((cudaError_t)e, "apply");
   ApplyParams Q3 = apply_base(p, 1, nrhs);        // w3 = C2 v into tmp[0] (t is dead now)
@@ -524,7 +539,7 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
   Q3.nterm = 1;
   Q3.nout = 1;
   Q3.out[0] = p->tmp[0];
-  set_mat(Q3, 0, C, 1.0, nullptr, 0.0, n1);
+  set_mat(Q3, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
   Q3.t_src[0] = 0; Q3.t_dst[0] = 0;
   if ((e = apply_launch(p, Q3, s))) return cuda_fail((cudaError_t)e, "apply");
   ApplyParams R = apply_base(p, 0, nrhs);         // s1 A1 w1, s2 C1 w2, s3 C1 w3, C1 w1
@@ -533,13 +548,13 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
   R.in[2] = p->tmp[0];
   R.nterm = 4;
   R.nout = 4;
-  set_mat(R, 0, A, s_[0], nullptr, 0.0, n1);
+  set_mat(R, 0, A, s_[0], nullptr, 0.0, n1, p->Aref, p->Crow);
   R.t_src[0] = 0; R.t_dst[0] = 0;
-  set_mat(R, 1, C, s_[1], nullptr, 0.0, n1);
+  set_mat(R, 1, C, s_[1], nullptr, 0.0, n1, p->Aref, p->Crow);
   R.t_src[1] = 1; R.t_dst[1] = 1;
-  set_mat(R, 2, C, s_[2], nullptr, 0.0, n1);
+  set_mat(R, 2, C, s_[2], nullptr, 0.0, n1, p->Aref, p->Crow);
   R.t_src[2] = 2; R.t_dst[2] = 2;
-  set_mat(R, 3, C, 1.0, nullptr, 0.0, n1);
+  set_mat(R, 3, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
   R.t_src[3] = 0; R.t_dst[3] = 3;
   R.dotv = lam;
   R.dots = dots;
@@ -628,7 +643,7 @@ int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, con
     return cuda_fail(ce, "device query");
   }
   int rc = FEM_FFT_OK;
-  reference_matrices(n, &p->Aref, &p->Cref);
+  reference_matrices(n, &p->Aref, &p->Cref, &p->Crow);
   for (int i = 0; i < N && !rc; ++i) {
     // identical axes share nothing on purpose: tables are small
     if (precompute_axis(n, (int)p->K[i], p->X[i], p->a[i], &p->ax[i])) rc = FEM_FFT_ERR_ASSUMPTION_A;
@@ -638,7 +653,7 @@ int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, con
     for (int i = 0; i < N && !rc; ++i) rc = upload_axis<float>(p, p->ax[i], &p->t32[i], s);
   const size_t field = (size_t)max_nrhs * p->dof;
   if (!rc && precision == FEM_FFT_MIXED) rc = dev_alloc(p, (void**)&p->w32, field * sizeof(float));
-  const int ntmp = N == 1 ? 0 : (N == 2 ? 2 : 4);
+  const int ntmp = N == 1 ? 0 : (N == 2 ? 3 : 4);
   for (int t = 0; t < ntmp && !rc; ++t) rc = dev_alloc(p, (void**)&p->tmp[t], field * sizeof(double));
   if (!rc) rc = dev_alloc(p, (void**)&p->d_scalars, 16 * sizeof(double));
   if (rc) {

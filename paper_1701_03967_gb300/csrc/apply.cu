@@ -7,10 +7,14 @@
 // is a sum of Kronecker products of these, so L u (and the residual
 // b - L u, and the bilinear forms lam^T (dL/da_i) u) are evaluated as a short
 // chain of 1D applications along the axes, e.g. in 2D
-//     t1 = calC_2 u, t2 = calA_2 u (axis 2), then
-//     L u = (a_1 s_1 calA_1 + c calC_1) t1 + a_2 s_2 calC_1 t2 (axis 1).
-// One thread computes one output position for all outputs of the launch;
-// inputs are read through the read-only cache (along strided axes the
+//     w = (a_1 s_1 calA_1 + c calC_1) u (axis 1), t = a_2 s_2 calA_2 u (axis 2),
+//     L u = calC_2 w + calC_1 t.
+// The stiffness factor of every term is applied to u itself and the mass
+// factors afterwards: a stiffness applied to an intermediate that carries
+// white rounding noise (such as calC_2 u) would amplify that noise by
+// ~4 h^-2 |A| and floor the refinement at ~6e-9 (2D, n = 9, K = 1024).
+// One thread computes the outputs of one element for all outputs of the
+// launch; inputs are read through the read-only cache (along strided axes the
 // threads of a warp cover consecutive positions of the contiguous axis).
 #include <cuda_runtime.h>
 
@@ -48,66 +52,124 @@ __device__ void block_accumulate(double (&v)[NV], double* dst) {
   }
 }
 
-template <int NORD>
+// One thread per (pencil position, element e): it produces the n outputs
+// owned by element e (its interior nodes and its right vertex).  Every element
+// product is evaluated in difference form, E u_e = E (u_e - u_e[0] 1) +
+// u_e[0] (E 1) with the EXACT row sums E 1: the stiffness rows annihilate
+// constants (Section 2, A (1..1)^T = 0), so the float64 products involve the
+// differences of neighbouring nodal values instead of the values themselves,
+// and the rounding of the entries of A (whose float64 row sums are ~1e-14,
+// not 0) cannot act as a spurious zeroth-order term 4 h^-2 (A 1) u, which
+// would shift the solution by ~6e-9 relative at K = 1024, n = 9.  For smooth u this removes
+// most of the cancellation of 4 h^-2 calA u (terms ~h^-2 |u|, result ~|u|),
+// which otherwise puts a rounding floor of ~1e-8 under the refined solution at
+// K = 1024, n = 9.
+template <int NORD, int NOUT>
 __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyParams P) {
   constexpr int N1 = NORD + 1;
   __shared__ double mats[kApplyMaxTerms][N1 * N1];
-  for (int t = 0; t < P.nterm; ++t)
+  __shared__ double rows1[kApplyMaxTerms][N1];     // exact E (1..1)^T
+  for (int t = 0; t < P.nterm; ++t) {
     for (int j = threadIdx.x; j < N1 * N1; j += blockDim.x) mats[t][j] = P.mats[t][j];
+    for (int r = threadIdx.x; r < N1; r += blockDim.x) rows1[t][r] = P.rows1[t][r];
+  }
   __syncthreads();
 
-  const long long total = P.outer * (long long)P.M * P.inner;
+  const int K = P.K;
+  const long long total = P.outer * (long long)K * P.inner;
   const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[kApplyMaxOut] = {0.0, 0.0, 0.0, 0.0};
+  double dotacc[kApplyMaxOut] = {0.0, 0.0, 0.0, 0.0};   // NOUT <= kApplyMaxOut
   double rr = 0.0, bb = 0.0;
   if (pos < total) {
     const long long w = pos % P.inner;
     const long long rest = pos / P.inner;
-    const int i = (int)(rest % P.M);
-    const long long o = rest / P.M;
+    const int e = (int)(rest % K);
+    const long long o = rest / K;
     const long long line = o * (long long)P.M * P.inner + w;   // offset of index 0 of this pencil
-    const int e = i / NORD;
-    const int s = i - e * NORD;
+    const bool has_node = e < K - 1;                           // right vertex is an unknown
+    double acc[NOUT][NORD];
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j)
+#pragma unroll
+      for (int r = 0; r < NORD; ++r) acc[j][r] = 0.0;
     for (int t = 0; t < P.nterm; ++t) {
       const double* x = P.in[P.t_src[t]];
       const double* E = mats[t];
-      double y = 0.0;
-      // row of the element matrix for this node within element e
-      const int row = (s < NORD - 1) ? s + 1 : NORD;
+      const double* E1 = rows1[t];
+      double ue[N1], un[N1];
 #pragma unroll
       for (int q = 0; q <= NORD; ++q) {
         int g = NORD * e + q - 1;
-        if (g >= 0 && g < P.M) y = fma(E[row * N1 + q], __ldg(&x[line + (long long)g * P.inner]), y);
+        ue[q] = (g >= 0 && g < P.M) ? __ldg(&x[line + (long long)g * P.inner]) : 0.0;
       }
-      if (s == NORD - 1) {   // a vertex also belongs to element e + 1 (local node 0)
+      if (has_node) {
 #pragma unroll
         for (int q = 0; q <= NORD; ++q) {
           int g = NORD * (e + 1) + q - 1;
-          if (g < P.M) y = fma(E[q], __ldg(&x[line + (long long)g * P.inner]), y);
+          un[q] = (g < P.M) ? __ldg(&x[line + (long long)g * P.inner]) : 0.0;
         }
       }
-      acc[P.t_dst[t]] += y;
-    }
-    if (P.dotv) {
-      const double lv = __ldg(&P.dotv[pos]);
+      const double u0 = ue[0], v0 = un[0];
 #pragma unroll
-      for (int j = 0; j < kApplyMaxOut; ++j) acc[j] *= lv;
-    } else {
-      for (int j = 0; j < P.nout; ++j) {
-        double v = acc[j];
-        if (j == 0 && P.base) {
-          double b = __ldg(&P.base[pos]);
-          v = b - v;
-          rr = v * v;
-          bb = b * b;
+      for (int q = 1; q <= NORD; ++q) {
+        ue[q] -= u0;
+        if (has_node) un[q] -= v0;
+      }
+      double y[NORD];
+#pragma unroll
+      for (int s = 0; s < NORD - 1; ++s) {        // interior node s+1 of element e
+        double v = u0 * E1[s + 1];
+#pragma unroll
+        for (int q = 1; q <= NORD; ++q) v = fma(E[(s + 1) * N1 + q], ue[q], v);
+        y[s] = v;
+      }
+      if (has_node) {                              // vertex: row n of e + row 0 of e+1
+        double v = u0 * E1[NORD] + v0 * E1[0];
+#pragma unroll
+        for (int q = 1; q <= NORD; ++q) v = fma(E[NORD * N1 + q], ue[q], v);
+#pragma unroll
+        for (int q = 1; q <= NORD; ++q) v = fma(E[q], un[q], v);
+        y[NORD - 1] = v;
+      } else {
+        y[NORD - 1] = 0.0;
+      }
+      const int d = P.t_dst[t];
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j)
+        if (j == d)
+#pragma unroll
+          for (int r = 0; r < NORD; ++r) acc[j][r] += y[r];
+    }
+    const int nrow = has_node ? NORD : NORD - 1;
+#pragma unroll
+    for (int r = 0; r < NORD; ++r) {
+      if (r >= nrow) break;
+      const long long off = line + (long long)(NORD * e + r) * P.inner;
+      if (P.dotv) {
+        const double lv = __ldg(&P.dotv[off]);
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) dotacc[j] = fma(acc[j][r], lv, dotacc[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) {
+          if (j < P.nout) {
+            double v = acc[j][r];
+            if (j == 0 && P.addend) v += P.addend[off];
+            if (j == 0 && P.base) {
+              double b = __ldg(&P.base[off]);
+              v = b - v;
+              rr = fma(v, v, rr);
+              bb = fma(b, b, bb);
+            }
+            if (j == 0 && P.out0_f32) P.out0_f32[off] = (float)v;
+            else P.out[j][off] = v;
+          }
         }
-        if (j == 0 && P.out0_f32) P.out0_f32[pos] = (float)v;
-        else P.out[j][pos] = v;
       }
     }
   }
   if (P.dotv) {
-    block_accumulate<kApplyMaxOut>(acc, P.dots);
+    block_accumulate<kApplyMaxOut>(dotacc, P.dots);
   } else if (P.norms) {
     double v2[2] = {rr, bb};
     block_accumulate<2>(v2, P.norms);
@@ -115,12 +177,16 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyParams P) {
 }
 
 int launch_apply(const ApplyParams& P, cudaStream_t s) {
-  const long long total = P.outer * (long long)P.M * P.inner;
+  const long long total = P.outer * (long long)P.K * P.inner;
   if (total <= 0) return 0;
   const long long blocks = (total + kApplyThreads - 1) / kApplyThreads;
   switch (P.n) {
-#define FEMFFT_APPLY_CASE(NN) \
-  case NN: apply_kernel<NN><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P); break;
+#define FEMFFT_APPLY_CASE(NN)                                                  \
+  case NN:                                                                     \
+    if (P.nout <= 1) apply_kernel<NN, 1><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P); \
+    else if (P.nout <= 2) apply_kernel<NN, 2><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P); \
+    else apply_kernel<NN, 4><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P); \
+    break;
     FEMFFT_APPLY_CASE(1) FEMFFT_APPLY_CASE(2) FEMFFT_APPLY_CASE(3) FEMFFT_APPLY_CASE(4)
     FEMFFT_APPLY_CASE(5) FEMFFT_APPLY_CASE(6) FEMFFT_APPLY_CASE(7) FEMFFT_APPLY_CASE(8)
     FEMFFT_APPLY_CASE(9)

@@ -21,8 +21,8 @@ struct AxisHost {
   std::vector<double> mu;      // [M] a * s * lam
   std::vector<double> tw;      // [2K] exp(-2 pi i j / K), (re, im) pairs
   std::vector<double> rot;     // [2K] exp(-i pi k / (2K))
-  std::vector<double> fwd;     // [K][n][n+1] per-k forward maps; k = 0: bubble map
-  std::vector<double> inv;     // [K][n+1][n] per-k inverse maps; k = 0: bubble map
+  std::vector<double> fwd;     // [K][n][2Q] per-k forward maps (Q = n/2+1); k = 0: bubble map
+  std::vector<double> inv;     // [K][2Q][n] per-k inverse maps; k = 0: bubble map
   std::vector<double> pvec;    // [K][n][n-1] p_k^(l) (k = 0: e^(l)), for tests
   std::vector<int> parity;     // [n-1] +1 even / -1 odd bubble eigenvector
 };
@@ -30,16 +30,17 @@ struct AxisHost {
 // Precompute the tables of one axis.  Returns 0 or a negative status.
 int precompute_axis(int n, int K, double X, double a, AxisHost* out);
 
-// Reference-element matrices rounded to double ((n+1)^2, row-major).
-void reference_matrices(int n, std::vector<double>* A, std::vector<double>* C);
+// Reference-element matrices rounded to double ((n+1)^2, row-major) and the
+// row sums of C (those of A are exactly zero).
+void reference_matrices(int n, std::vector<double>* A, std::vector<double>* C, std::vector<double>* Crow);
 
 // Device view of one axis for one precision T (float or double).
 struct AxisDev {
   int n, K, M;
   const void* tw;    // T2 [K]
   const void* rot;   // T2 [K]
-  const void* fwd;   // T [K][n][n+1]
-  const void* inv;   // T [K][n+1][n]
+  const void* fwd;   // T [K][n][2Q]
+  const void* inv;   // T [K][2Q][n]
   const void* mu;    // T [M]
 };
 

@@ -27,7 +27,13 @@ struct ApplyParams {
   int nterm, nout;
   int t_src[kApplyMaxTerms], t_dst[kApplyMaxTerms];
   double mats[kApplyMaxTerms][kApplyMatMax];
-  // residual form for output 0: out0 = base - sum (base != null)
+  // exact row sums E (1..1)^T of every term matrix (the stiffness rows sum to
+  // zero exactly; float64 rounding of A does not preserve that)
+  double rows1[kApplyMaxTerms][kMaxOrder + 1];
+  // output 0 = addend + sum of its terms (addend may alias out[0]: every
+  // thread reads and writes only its own positions); residual form:
+  // output 0 = base - (addend + sum) when base != null
+  const double* addend;
   const double* base;
   float* out0_f32;               // if set, output 0 is written as float32 here
   double* norms;                 // if set: += ||out0||^2 (norms[0]), ||base||^2 (norms[1])

@@ -72,9 +72,16 @@ __device__ __forceinline__ cpx<T> ld_cpx(const void* base, int idx) {
 enum PassMode { MODE_FWD = 0, MODE_INV = 1, MODE_FUSED = 2 };
 
 constexpr int kMaxV = 12;          // FFT values held per thread
-constexpr int kMaxChunkTasks = 16; // chunks per thread in the sequence build
+constexpr int kMaxChunkTasks = 8;  // chunks per thread in the sequence build
 constexpr int kMaxRadixPasses = 16;
-constexpr int kPencilThreads = 256; // threads per CTA of the pencil passes
+constexpr int kPencilThreads = 512; // threads per CTA of the float pencil passes
+constexpr int kPencilThreads64 = 256; // threads per CTA of the double pencil passes
+template <typename T>
+__host__ __device__ constexpr int pencil_threads() { return sizeof(T) == 8 ? kPencilThreads64 : kPencilThreads; }
+constexpr int kMaxW = 32;           // pencils per CTA (float)
+constexpr int kMaxW64 = 12;         // pencils per CTA (double)
+template <typename T>
+__host__ __device__ constexpr int max_w() { return sizeof(T) == 8 ? kMaxW64 : kMaxW; }
 
 struct PassParams {
   const void* in;
@@ -378,7 +385,7 @@ template <typename T, int NORD>
 __device__ __forceinline__ T pencil_den_base(const PassParams& P, int p) {
   // c + sum over the other axes of a_j mu_j[sigma_j] for the pencil p of this
   // CTA (fused pass on axis 0: the pencil index is the flat index of the
-  // later axes).
+  // later axes), summed in float64.
   const PassGeom& g = P.g;
   long long w = 0;    // inner == 1: the later axes (if any) all have size 1
   if (g.inner > 1) {
@@ -398,187 +405,183 @@ __device__ __forceinline__ T pencil_den_base(const PassParams& P, int p) {
   return T(base);
 }
 
-// Per frequency pair (k, K-k): forward post-twiddle and n x (n+1) maps
-// (MODE_FWD: write spectral coefficients), optionally the divide and the
-// inverse maps and pre-twiddle (MODE_FUSED); MODE_INV starts from spectral
-// coefficients in shared memory.
-template <typename T, int NORD, int MODE>
-__device__ void spectral_stage(cpx<T>* sm, const PassParams& P) {
+// Post-twiddle of the forward DCT-II (in place).  For the frequency pair
+// (k, K-k) and sequence q, with A = exp(-i phi_k) V_k and
+// B = exp(+i phi_k) V_{K-k}:  chunk k <- (2 S_q(k), 2 C_q(k)) =
+// (Im B - Im A, Im A + Im B), chunk K-k <- (2 S_q(K-k), 2 C_q(K-k)) =
+// (Re A + Re B, Re A - Re B).  Chunk 0 already holds (S_q(K), C_q(0)) =
+// (Re V_0, Im V_0).
+template <typename T, int NORD>
+__device__ void post_twiddle(cpx<T>* sm, const PassParams& P) {
   constexpr int Q = NORD / 2 + 1;
-  constexpr int QC = (NORD - 1) / 2 + 1;
-  constexpr int N1 = NORD + 1;
   const int K = P.ax.K;
-  const int npairs = K / 2 + 1;
-  const T* F = reinterpret_cast<const T*>(P.ax.fwd);
-  const T* I = reinterpret_cast<const T*>(P.ax.inv);
-  const T* mu = reinterpret_cast<const T*>(P.ax.mu);
-  const int ntask = P.g.W * npairs;
+  const int npairs = K / 2;
+  const int ntask = P.g.W * npairs * Q;
   for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-    const int p = task / npairs;
-    const int k = task - p * npairs;
+    const int q = task % Q;
+    const int r = task / Q;
+    const int k = 1 + r % npairs;
+    const int p = r / npairs;
     cpx<T>* pen = sm + p * P.pitch;
-    T* penr = reinterpret_cast<T*>(pen);
-    T wk[NORD], wkk[NORD];       // spectral values of k and K-k
-    const int kk = (k == 0) ? 0 : K - k;
-    if (MODE == MODE_FWD || MODE == MODE_FUSED) {
-      if (k == 0) {
-        T in[N1];
+    const int kk = K - k;
+    const cpx<T> rk = ld_cpx<T>(P.ax.rot, k);
+    const cpx<T> A = cmul(rk, pen[k * Q + q]);
+    const cpx<T> B = cmul(cpx<T>{rk.re, -rk.im}, pen[kk * Q + q]);
+    pen[k * Q + q] = {B.im - A.im, A.im + B.im};
+    if (kk != k) pen[kk * Q + q] = {A.re + B.re, A.re - B.re};
+  }
+  __syncthreads();
+}
+
+// Per-frequency forward maps (Theorem 2, item 2): coefficient (k, l) =
+// F_k[l] . (chunk k slots), for every pencil of the CTA; optionally divided
+// by the spectral denominator.  One thread per (k, l) loads the map row once
+// (coalesced) and applies it to all W pencils.  Rounds cover whole
+// frequencies so that every chunk is read completely before it is rewritten.
+template <typename T, int NORD, bool DIVIDE>
+__device__ void forward_map(cpx<T>* sm, const PassParams& P, const T* base) {
+  constexpr int Q2 = 2 * (NORD / 2 + 1);
+  const int K = P.ax.K;
+  const int W = P.g.W;
+  const T* F = reinterpret_cast<const T*>(P.ax.fwd);
+  const T* mu = reinterpret_cast<const T*>(P.ax.mu);
+  const int kpr = blockDim.x / NORD;
+  const int kl = threadIdx.x / NORD, l = threadIdx.x - kl * NORD;
+  for (int k0 = 0; k0 < K; k0 += kpr) {
+    const int k = k0 + kl;
+    const bool act = kl < kpr && k < K && !(k == 0 && l == NORD - 1);
+    constexpr int WM = max_w<T>();
+    T out[WM];
+    if (act) {
+      T f[Q2];
 #pragma unroll
-        for (int q = 1; q < Q; ++q) in[q - 1] = pen[q].re;          // S_m(K)
+      for (int j = 0; j < Q2; ++j) f[j] = __ldg(&F[((size_t)k * NORD + l) * Q2 + j]);
+      const int sigma = (k == 0) ? l : NORD * k - 1 + l;
+      const T m = DIVIDE ? __ldg(&mu[sigma]) : T(0);
 #pragma unroll
-        for (int q = 1; q < QC; ++q) in[Q - 1 + q - 1] = pen[q].im; // C_m(0)
-#pragma unroll
-        for (int l = 0; l < NORD - 1; ++l) {
+      for (int p = 0; p < WM; ++p) {
+        if (p < W) {
+          const T* ch = reinterpret_cast<const T*>(sm + p * P.pitch) + k * Q2;
           T acc = T(0);
 #pragma unroll
-          for (int j = 0; j < NORD - 1; ++j) acc += __ldg(&F[l * N1 + j]) * in[j];
-          wk[l] = acc;
-        }
-      } else {
-        cpx<T> rk = ld_cpx<T>(P.ax.rot, k);     // exp(-i phi_k)
-        cpx<T> rkc = {rk.re, -rk.im};
-        T ink[N1], inkk[N1];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          cpx<T> A = cmul(rk, pen[k * Q + q]);
-          cpx<T> B = cmul(rkc, pen[kk * Q + q]);
-          ink[q] = B.im - A.im;                 // 2 S(k)
-          inkk[q] = A.re + B.re;                // 2 S(K-k)
-          if (q < QC) {
-            ink[Q + q] = A.im + B.im;           // 2 C(k)
-            inkk[Q + q] = A.re - B.re;          // 2 C(K-k)
-          }
-        }
-        const T* Fk = F + (size_t)k * NORD * N1;
-        const T* Fkk = F + (size_t)kk * NORD * N1;
-#pragma unroll
-        for (int l = 0; l < NORD; ++l) {
-          T a = T(0), b = T(0);
-#pragma unroll
-          for (int j = 0; j < N1; ++j) {
-            a += __ldg(&Fk[l * N1 + j]) * ink[j];
-            b += __ldg(&Fkk[l * N1 + j]) * inkk[j];
-          }
-          wk[l] = a;
-          wkk[l] = b;
-        }
-      }
-    } else {   // MODE_INV: read spectral values
-      if (k == 0) {
-#pragma unroll
-        for (int l = 0; l < NORD - 1; ++l) wk[l] = penr[1 + l];
-      } else {
-#pragma unroll
-        for (int l = 0; l < NORD; ++l) {
-          wk[l] = penr[k * 2 * Q + l];
-          wkk[l] = penr[kk * 2 * Q + l];
+          for (int j = 0; j < Q2; ++j) acc += f[j] * ch[j];
+          if (DIVIDE) acc = acc / (base[p] + m);
+          out[p] = acc;
         }
       }
     }
-    if (MODE == MODE_FWD) {
-      if (k == 0) {
+    __syncthreads();
+    if (act) {
+      const int slot = (k == 0) ? l + 1 : l;
 #pragma unroll
-        for (int l = 0; l < NORD - 1; ++l) penr[1 + l] = wk[l];
-      } else {
-#pragma unroll
-        for (int l = 0; l < NORD; ++l) {
-          penr[k * 2 * Q + l] = wk[l];
-          if (kk != k) penr[kk * 2 * Q + l] = wkk[l];
-        }
-      }
-      continue;
+      for (int p = 0; p < WM; ++p)
+        if (p < W) reinterpret_cast<T*>(sm + p * P.pitch)[k * Q2 + slot] = out[p];
     }
-    if (MODE == MODE_FUSED) {
-      T base = pencil_den_base<T, NORD>(P, p);
-      if (k == 0) {
+    __syncthreads();
+  }
+}
+
+// Per-frequency inverse maps (Theorem 2, item 1): chunk k slot j <- I_k[j] .
+// w_k, where w_k are the n spectral values of frequency k (slots 0..n-1, or
+// 1..n-1 for the bubble modes of k = 0).  Slot 2q receives half the sine
+// coefficient a_q, slot 2q+1 half the cosine coefficient b_q of sequence q.
+template <typename T, int NORD>
+__device__ void inverse_map(cpx<T>* sm, const PassParams& P) {
+  constexpr int Q2 = 2 * (NORD / 2 + 1);
+  const int K = P.ax.K;
+  const int W = P.g.W;
+  const T* I = reinterpret_cast<const T*>(P.ax.inv);
+  const int kpr = blockDim.x / Q2;
+  const int kl = threadIdx.x / Q2, j = threadIdx.x - kl * Q2;
+  for (int k0 = 0; k0 < K; k0 += kpr) {
+    const int k = k0 + kl;
+    const bool act = kl < kpr && k < K;
+    constexpr int WM = max_w<T>();
+    T out[WM];
+    if (act) {
+      T f[NORD];
 #pragma unroll
-        for (int l = 0; l < NORD - 1; ++l) wk[l] = wk[l] / (base + __ldg(&mu[l]));
-      } else {
+      for (int l = 0; l < NORD; ++l) f[l] = __ldg(&I[((size_t)k * Q2 + j) * NORD + l]);
+      const int off = (k == 0) ? 1 : 0;
+      const int nl = (k == 0) ? NORD - 1 : NORD;
 #pragma unroll
-        for (int l = 0; l < NORD; ++l) {
-          wk[l] = wk[l] / (base + __ldg(&mu[NORD * k - 1 + l]));
-          wkk[l] = wkk[l] / (base + __ldg(&mu[NORD * kk - 1 + l]));
-        }
-      }
-    }
-    // inverse maps and pre-twiddle
-    if (k == 0) {
-      // H_0 = a(K) + i b(0): bubble parts only (node coefficients vanish)
-      cpx<T> H[Q];
-      H[0] = {T(0), T(0)};
+      for (int p = 0; p < WM; ++p) {
+        if (p < W) {
+          const T* ch = reinterpret_cast<const T*>(sm + p * P.pitch) + k * Q2 + off;
+          T acc = T(0);
 #pragma unroll
-      for (int q = 1; q < Q; ++q) {
-        T a = T(0), b = T(0);
-#pragma unroll
-        for (int l = 0; l < NORD - 1; ++l) {
-          a += __ldg(&I[(q - 1) * NORD + l]) * wk[l];
-          if (q < QC) b += __ldg(&I[(Q - 1 + q - 1) * NORD + l]) * wk[l];
-        }
-        H[q] = {a, b};
-      }
-#pragma unroll
-      for (int q = 0; q < Q; ++q) pen[q] = H[q];
-    } else {
-      const T* Ik = I + (size_t)k * N1 * NORD;
-      const T* Ikk = I + (size_t)kk * N1 * NORD;
-      T ak[N1], akk[N1];
-#pragma unroll
-      for (int j = 0; j < N1; ++j) {
-        T a = T(0), b = T(0);
-#pragma unroll
-        for (int l = 0; l < NORD; ++l) {
-          a += __ldg(&Ik[j * NORD + l]) * wk[l];
-          b += __ldg(&Ikk[j * NORD + l]) * wkk[l];
-        }
-        ak[j] = a;
-        akk[j] = b;
-      }
-      cpx<T> rk = ld_cpx<T>(P.ax.rot, k);       // exp(-i phi_k)
-      // exp(-i phi_{K-k}) = -i exp(+i phi_k)
-      cpx<T> rkk = cmi(cpx<T>{rk.re, -rk.im});
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        T bk = (q < QC) ? ak[Q + q] : T(0);
-        T bkk = (q < QC) ? akk[Q + q] : T(0);
-        cpx<T> Hk = cmul(rk, cpx<T>{akk[q] - bkk, ak[q] + bk});
-        pen[k * Q + q] = Hk;
-        if (kk != k) {
-          cpx<T> Hkk = cmul(rkk, cpx<T>{ak[q] - bk, akk[q] + bkk});
-          pen[kk * Q + q] = Hkk;
+          for (int l = 0; l < NORD; ++l)
+            if (l < nl) acc += f[l] * ch[l];
+          out[p] = acc;
         }
       }
     }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+      for (int p = 0; p < WM; ++p)
+        if (p < W) reinterpret_cast<T*>(sm + p * P.pitch)[k * Q2 + j] = out[p];
+    }
+    __syncthreads();
+  }
+}
+
+// Pre-twiddle of the inverse DCT-III (in place).  With a_q, b_q the halved
+// sine/cosine coefficients in slots (2q, 2q+1) of chunks k and K-k:
+//   H_k     = exp(-i phi_k)     [(a(K-k) - b(K-k)) + i (a(k) + b(k))],
+//   H_{K-k} = exp(-i phi_{K-k}) [(a(k) - b(k)) + i (a(K-k) + b(K-k))],
+// exp(-i phi_{K-k}) = -i exp(+i phi_k).  Chunk 0 already holds
+// H_0 = a_q(K) + i b_q(0).
+template <typename T, int NORD>
+__device__ void pre_twiddle(cpx<T>* sm, const PassParams& P) {
+  constexpr int Q = NORD / 2 + 1;
+  const int K = P.ax.K;
+  const int npairs = K / 2;
+  const int ntask = P.g.W * npairs * Q;
+  for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+    const int q = task % Q;
+    const int r = task / Q;
+    const int k = 1 + r % npairs;
+    const int p = r / npairs;
+    cpx<T>* pen = sm + p * P.pitch;
+    const int kk = K - k;
+    const cpx<T> rk = ld_cpx<T>(P.ax.rot, k);
+    const cpx<T> vk = pen[k * Q + q];      // (a(k), b(k))
+    const cpx<T> vkk = pen[kk * Q + q];    // (a(K-k), b(K-k))
+    pen[k * Q + q] = cmul(rk, cpx<T>{vkk.re - vkk.im, vk.re + vk.im});
+    if (kk != k) pen[kk * Q + q] = cmul(cmi(cpx<T>{rk.re, -rk.im}), cpx<T>{vk.re - vk.im, vkk.re + vkk.im});
   }
   __syncthreads();
 }
 
 template <typename T, int NORD, int MODE>
-__global__ void __launch_bounds__(kPencilThreads, 1) pencil_pass_kernel(PassParams P) {
+__global__ void __launch_bounds__(pencil_threads<T>(), 1) pencil_pass_kernel(PassParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T base[kMaxW];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   T* smr = reinterpret_cast<T*>(smem_raw);
   constexpr int Q = NORD / 2 + 1;
+  if (MODE == MODE_FUSED && threadIdx.x < P.g.W) base[threadIdx.x] = pencil_den_base<T, NORD>(P, threadIdx.x);
   if (MODE == MODE_INV) {
     load_tile<T, NORD>(smr, P, true);
     __syncthreads();
-    spectral_stage<T, NORD, MODE_INV>(sm, P);
-    fft_all<T>(sm, P, P.g.W * Q, Q, false, true);
-    reconstruct<T, NORD>(sm, P);
-    store_tile<T, NORD>(smr, P, false);
   } else {
     load_tile<T, NORD>(smr, P, false);
     __syncthreads();
     build_sequences<T, NORD>(sm, P);
     fft_all<T>(sm, P, P.g.W * Q, Q, true, false);
-    spectral_stage<T, NORD, MODE>(sm, P);
+    post_twiddle<T, NORD>(sm, P);
+    forward_map<T, NORD, MODE == MODE_FUSED>(sm, P, base);
     if (MODE == MODE_FWD) {
       store_tile<T, NORD>(smr, P, true);
-    } else {
-      fft_all<T>(sm, P, P.g.W * Q, Q, false, true);
-      reconstruct<T, NORD>(sm, P);
-      store_tile<T, NORD>(smr, P, false);
+      return;
     }
   }
+  inverse_map<T, NORD>(sm, P);
+  pre_twiddle<T, NORD>(sm, P);
+  fft_all<T>(sm, P, P.g.W * Q, Q, false, true);
+  reconstruct<T, NORD>(sm, P);
+  store_tile<T, NORD>(smr, P, false);
 }
 
 }  // namespace femfft

@@ -149,7 +149,7 @@ static void reference_matrices_dd(int n, std::vector<dd>* A, std::vector<dd>* C)
     }
 }
 
-void reference_matrices(int n, std::vector<double>* A, std::vector<double>* C) {
+void reference_matrices(int n, std::vector<double>* A, std::vector<double>* C, std::vector<double>* Crow) {
   std::vector<dd> Ad, Cd;
   reference_matrices_dd(n, &Ad, &Cd);
   A->resize(Ad.size());
@@ -157,6 +157,15 @@ void reference_matrices(int n, std::vector<double>* A, std::vector<double>* C) {
   for (size_t i = 0; i < Ad.size(); ++i) {
     (*A)[i] = Ad[i].to_double();
     (*C)[i] = Cd[i].to_double();
+  }
+  if (Crow) {
+    // row sums of C in double-double (those of A are exactly zero)
+    Crow->assign(n + 1, 0.0);
+    for (int r = 0; r <= n; ++r) {
+      dd acc(0.0);
+      for (int q = 0; q <= n; ++q) acc += Cd[r * (n + 1) + q];
+      (*Crow)[r] = acc.to_double();
+    }
   }
 }
 
@@ -287,8 +296,9 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
   ax.mu.assign(M, 0.0);
   ax.tw.assign(2 * K, 0.0);
   ax.rot.assign(2 * K, 0.0);
-  ax.fwd.assign((size_t)K * n * n1, 0.0);
-  ax.inv.assign((size_t)K * n1 * n, 0.0);
+  const int Q2 = 2 * Q;              // reals per chunk: (sine, cosine) pairs
+  ax.fwd.assign((size_t)K * n * Q2, 0.0);
+  ax.inv.assign((size_t)K * Q2 * n, 0.0);
   ax.pvec.assign((size_t)K * n * std::max(n - 1, 1), 0.0);
   ax.parity.assign(std::max(n - 1, 0), 0);
 
@@ -312,9 +322,11 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
         Ct[i * m + j] = C[(i + 1) * n1 + (j + 1)];
       }
     if (sym_def_eig(m, At, Ct, &lam0, &E)) return -2;
-    // Section 2, Lemma 1: each e^(l) is even or odd
-    double* fb = &ax.fwd[0];   // [n-1][n-1] with row stride n+1
-    double* ib = &ax.inv[0];   // [n-1][n-1] with row stride n
+    // Section 2, Lemma 1: each e^(l) is even or odd.  Chunk 0 after the FFT
+    // holds, for sequence q, slot 2q = S_q(K) (alternating sum) and slot
+    // 2q+1 = C_q(0) (plain sum); the bubble maps read/write these slots.
+    double* fb = &ax.fwd[0];   // [n-1][2Q]
+    double* ib = &ax.inv[0];   // [2Q][n]  (columns l = 0..n-2)
     for (int l = 0; l < m; ++l) {
       double de = 0.0, dodd = 0.0;
       for (int i = 0; i < m; ++i) {
@@ -327,21 +339,16 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
       ax.lam[l] = lam0[l].to_double();
       ax.cnorm[l] = double(K);
       for (int i = 0; i < m; ++i) ax.pvec[(size_t)l * (n - 1) + i] = E[i * m + l].to_double();
-      // forward bubble map: inputs [S_1..S_{Q-1}, C_1..C_{QC-1}] at k = K / k = 0
-      // y_0l = (1/K) sum_m e[m] S_m(K)   (even e)   or   sum_m e[m] C_m(0)  (odd e)
-      // inverse bubble map: outputs a_m(K) = b_e[m], b_m(0) = b_o[m]
+      // forward: y_0l = (1/K) sum_m e[m] S_m(K) (even e) or sum_m e[m] C_m(0) (odd e)
+      // inverse: a_m(K) = b_e[m], b_m(0) = b_o[m] with b = sum_l w_0l e^(l)
       for (int q = 1; q < Q; ++q) {
         double em = E[(q - 1) * m + l].to_double();
         if (par > 0) {
-          fb[l * n1 + (q - 1)] = em / K;
-          ib[(q - 1) * n + l] = em;
-        }
-      }
-      for (int q = 1; q < QC; ++q) {
-        double em = E[(q - 1) * m + l].to_double();
-        if (par < 0) {
-          fb[l * n1 + (Q - 1) + (q - 1)] = em / K;
-          ib[((Q - 1) + (q - 1)) * n + l] = em;
+          fb[l * Q2 + 2 * q] = em / K;
+          ib[(2 * q) * n + l] = em;
+        } else if (q < QC) {
+          fb[l * Q2 + 2 * q + 1] = em / K;
+          ib[(2 * q + 1) * n + l] = em;
         }
       }
     }
@@ -369,8 +376,8 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
     }
     if (sym_def_eig(n, At, Ct, &lamk, &Z)) return -2;
     double cphi = chh.to_double(), sphi = sh.to_double();
-    double* F = &ax.fwd[(size_t)k * n * n1];
-    double* I = &ax.inv[(size_t)k * n1 * n];
+    double* F = &ax.fwd[(size_t)k * n * Q2];
+    double* I = &ax.inv[(size_t)k * Q2 * n];
     for (int l = 0; l < n; ++l) {
       dd z0 = Z[0 * n + l];
       if (z0.hi == 0.0) return -2;
@@ -385,28 +392,27 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
       ax.cnorm[sig] = nrm.to_double();
       for (int i = 0; i < n - 1; ++i) ax.pvec[((size_t)k * n + l) * (n - 1) + i] = z[i + 1].to_double();
       // p_e[m] = (p[m] + p[n-m]) / 2, p_o[m] = (p[m] - p[n-m]) / 2 (1-based m;
-      // p[m] = z[m])
-      dd inv_n = dd(1.0) / nrm;
-      // forward map row l (the 1/2 of the post-twiddle combination folded in):
+      // p[m] = z[m]).  Inputs of the forward map at chunk k: slot 2q = 2 S_q(k),
+      // slot 2q+1 = 2 C_q(k) (the post-twiddle combination is left doubled):
       //   S_0: cos(phi)/(4N), S_m: cos(phi) p_e[m] / N,
-      //   C_0: sin(phi)/(4N), C_m: -sin(phi) p_o[m] / N
-      F[l * n1 + 0] = (chh * inv_n * dd(0.25)).to_double();
-      F[l * n1 + Q] = (sh * inv_n * dd(0.25)).to_double();
-      // inverse map column l (the 1/2 of the pre-twiddle combination folded in):
-      //   a_0: cos(phi)/2, a_m: cos(phi) p_e[m], b_0: sin(phi)/2, b_m: -sin(phi) p_o[m]
+      //   C_0: sin(phi)/(4N), C_m: -sin(phi) p_o[m] / N.
+      // Outputs of the inverse map at chunk k: slot 2q = a_q / 2, slot 2q+1 =
+      // b_q / 2 (the half of the pre-twiddle combination folded in):
+      //   a_0: cos(phi)/2, a_m: cos(phi) p_e[m], b_0: sin(phi)/2, b_m: -sin(phi) p_o[m].
+      dd inv_n = dd(1.0) / nrm;
+      F[l * Q2 + 0] = (chh * inv_n * dd(0.25)).to_double();
+      F[l * Q2 + 1] = (sh * inv_n * dd(0.25)).to_double();
       I[0 * n + l] = 0.5 * cphi;
-      I[Q * n + l] = 0.5 * sphi;
+      I[1 * n + l] = 0.5 * sphi;
       for (int q = 1; q < Q; ++q) {
-        int mm = q;   // 1-based component
-        dd pe = (z[mm] + z[n - mm]) * dd(0.5);
-        F[l * n1 + q] = (chh * pe * inv_n).to_double();
-        I[q * n + l] = (chh * pe).to_double();
-      }
-      for (int q = 1; q < QC; ++q) {
-        int mm = q;
-        dd po = (z[mm] - z[n - mm]) * dd(0.5);
-        F[l * n1 + Q + q] = (-(sh * po * inv_n)).to_double();
-        I[(Q + q) * n + l] = (-(sh * po)).to_double();
+        dd pe = (z[q] + z[n - q]) * dd(0.5);
+        F[l * Q2 + 2 * q] = (chh * pe * inv_n).to_double();
+        I[(2 * q) * n + l] = (chh * pe).to_double();
+        if (q < QC) {
+          dd po = (z[q] - z[n - q]) * dd(0.5);
+          F[l * Q2 + 2 * q + 1] = (-(sh * po * inv_n)).to_double();
+          I[(2 * q + 1) * n + l] = (-(sh * po)).to_double();
+        }
       }
     }
     (void)theta;

@@ -1,0 +1,44 @@
+"""Full-size parity: the solver on the benchmark-scale workloads against the
+FP64 oracle solved at the same full size (dense Theorem-1 eigenbasis
+products on the host), on the same seeded N(0,1) right-hand sides, in the
+launch configuration the benchmark times (default plans, max_nrhs = 1).
+
+2D: n = 9, K = 1024 x 1024 on [0,1]x[0,2], a = (1, 2.5), c = 1 (84.9 M DOF).
+3D: n = 9, K = 64^3 (190.1 M DOF) and n = 4, K = 128^3 (133.4 M DOF), unit cube,
+    a = (1,1,1), c = 0.
+Tolerances: relative L2 1e-12 (FP64 path) and 1e-10 (mixed path after its
+default refinement)."""
+
+import numpy as np
+import pytest
+
+from oracle import solve as osolve
+from paper_1701_03967_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WORKLOADS = [
+    ("2d_n9_K1024", dict(n=9, K=(1024, 1024), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0), synth.CFG_LARGE_2D),
+    ("3d_n9_K64", dict(n=9, K=(64, 64, 64), X=(1.0, 1.0, 1.0), a=(1.0, 1.0, 1.0), c=0.0), synth.CFG_3D),
+    ("3d_n4_K128", dict(n=4, K=(128, 128, 128), X=(1.0, 1.0, 1.0), a=(1.0, 1.0, 1.0), c=0.0), synth.CFG_3D),
+]
+
+
+@pytest.mark.parametrize("name,wl,cfg", WORKLOADS, ids=[w[0] for w in WORKLOADS])
+def test_fullsize_fp64_and_mixed_match_oracle(name, wl, cfg):
+    from paper_1701_03967_gb300 import Plan
+    prob = osolve.Problem(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"])
+    b = synth.normal_field(prob.M, cfg, 0, 1 if len(wl["K"]) == 3 and wl["n"] == 4 else 0)
+    want = osolve.solve(prob, b)
+    nrm = np.linalg.norm(want)
+    bt = torch.from_numpy(b).cuda()
+    for precision, tol in (("fp64", 1e-12), ("mixed", 1e-10)):
+        plan = Plan(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"], precision=precision)
+        got = plan.solve(bt).cpu().numpy()
+        plan.close()
+        rel = float(np.linalg.norm(got - want) / nrm)
+        print(f"{name} {precision} rel err {rel:.3e}")
+        assert rel <= tol, (name, precision, rel)
+        del got
+    torch.cuda.empty_cache()
