@@ -52,6 +52,7 @@ def lib():
         "fem_fft_axis_precompute": ([i32, i64, f64, PD, PD, PD], i32),
         "fem_fft_profile": ([vp, i32], i32),
         "fem_fft_profile_read": ([vp, i32, P64, PD, PD, PD], i32),
+        "fem_fft_apply_noalloc": ([i32, i32, P64, PD, PD, f64, vp, vp, i64, vp], i32),
         "fem_fft_strerror": ([i32], ctypes.c_char_p),
         "fem_fft_last_error": ([], ctypes.c_char_p),
     }

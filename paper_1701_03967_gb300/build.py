@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfemfft.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["pencil_f64.cu", "pencil_f32.cu", "apply.cu", "api.cu"]
+CU_SOURCES = ["pencil_f64.cu", "pencil_f32.cu", "apply.cu", "api.cu", "noalloc.cu"]
 CPP_SOURCES = ["precompute.cpp"]
 
 
