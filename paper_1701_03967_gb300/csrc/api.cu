@@ -47,8 +47,11 @@ bool valid_K(int64_t K) {
   return K == 1;
 }
 
-// FFT schedule for length K: values per thread V and radix sequence.
-void fft_schedule(int K, int* V, int* npass, int* radix) {
+// FFT schedule for length K: values per thread V and radix sequence (every
+// radix divides V; V <= kMaxV).  Powers of two: radix 8 (then 4 or 2) with 8
+// values per thread; K with a factor 3: radix 3 with 12 (or 6) values.
+void fft_schedule(int K, bool f64, int* V, int* npass, int* radix) {
+  (void)f64;
   int a = 0, b = 0, k = K;
   while (k % 2 == 0) { k /= 2; ++a; }
   while (k % 3 == 0) { k /= 3; ++b; }
@@ -64,17 +67,15 @@ void fft_schedule(int K, int* V, int* npass, int* radix) {
       *V = 6;
       if (aa) r.push_back(2);
     }
+  } else if (a >= 3) {
+    *V = 8;
+    int aa = a;
+    while (aa >= 3) { r.push_back(8); aa -= 3; }
+    if (aa == 2) r.push_back(4);
+    if (aa == 1) r.push_back(2);
   } else {
-    if (a >= 3) {
-      *V = 8;
-      int aa = a;
-      while (aa >= 3) { r.push_back(8); aa -= 3; }
-      if (aa == 2) r.push_back(4);
-      if (aa == 1) r.push_back(2);
-    } else {
-      *V = K;          // K = 2 or 4
-      r.push_back(K);
-    }
+    *V = K;          // K = 2 or 4
+    r.push_back(K);
   }
   *npass = (int)r.size();
   for (size_t i = 0; i < r.size(); ++i) radix[i] = r[i];
@@ -188,18 +189,28 @@ struct PassPlan {
 };
 
 // Pencils per CTA and the CTA grid for a pass over [outer][M][inner].
-int plan_pass(fem_fft_plan p, int axis, long long outer, long long inner, bool f64, PassPlan* pp) {
+int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inner, bool f64, PassPlan* pp) {
   const int n = p->n, K = (int)p->K[axis], M = (int)p->M[axis];
   const int Q = n / 2 + 1;
   const size_t csize = f64 ? 2 * sizeof(double) : 2 * sizeof(float);
   PassParams& P = pp->P;
   std::memset(&P, 0, sizeof(P));
-  fft_schedule(K, &P.V, &P.npass, P.radix);
-  int pitch = K * Q;
+  fft_schedule(K, f64, &P.V, &P.npass, P.radix);
+  int pitch = pencil_pitch_min(K, Q);   // chunks plus bank padding
   if (pitch % 2 == 0) pitch += 1;      // odd pitch spreads pencils over banks
   P.pitch = pitch;
   const size_t per_pen = (size_t)pitch * csize;
-  const size_t budget = (size_t)std::min(p->smem_optin, 220 * 1024);
+  const size_t tables = 2 * (size_t)K * csize;   // twiddles and rotations staged in shared memory
+  // shared memory per CTA: float passes keep two CTAs resident per SM
+  const size_t per_sm = 226 * 1024;
+  const int ctas = (f64 || mode == MODE_FUSED) ? 1 : kPencilCtasPerSm;
+  const size_t cta_budget = ctas == 1 ? (size_t)std::min(p->smem_optin, 220 * 1024)
+                                      : std::min<size_t>(p->smem_optin, per_sm / ctas - 1024);
+  if (cta_budget <= tables + per_pen) {
+    g_last_error = "pencil does not fit in shared memory";
+    return FEM_FFT_ERR_ARG;
+  }
+  const size_t budget = cta_budget - tables;
   long long wmax = (long long)(budget / per_pen);
   wmax = std::min<long long>(wmax, f64 ? kMaxW64 : kMaxW);
   if (wmax < 1) {
@@ -219,11 +230,14 @@ int plan_pass(fem_fft_plan p, int axis, long long outer, long long inner, bool f
     long long want = std::max<long long>(1, outer / (2 * 152));
     W = std::min(wmax, want);
   } else {
-    W = std::min<long long>(wmax, inner);
-    if (W >= 8) W = W / 8 * 8;
+    // strided pencils: a power of two (the tile loaders map thread -> pencil
+    // by t mod W)
+    long long lim = std::min<long long>(wmax, inner);
+    W = 1;
+    while (W * 2 <= lim) W *= 2;
     long long tiles = outer * ((inner + W - 1) / W);
     while (W > 1 && tiles < 2 * 152) {
-      W = std::max<long long>(1, W / 2);
+      W /= 2;
       tiles = outer * ((inner + W - 1) / W);
     }
   }
@@ -247,7 +261,7 @@ int plan_pass(fem_fft_plan p, int axis, long long outer, long long inner, bool f
   P.ax.fwd = d.fwd;
   P.ax.inv = d.inv;
   P.ax.mu = d.mu;
-  pp->smem = (size_t)W * per_pen;
+  pp->smem = (size_t)W * per_pen + tables;
   pp->threads = threads;
   return FEM_FFT_OK;
 }
@@ -258,7 +272,7 @@ int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const
   for (int j = 0; j < axis; ++j) outer *= p->M[j];
   for (int j = axis + 1; j < p->N; ++j) inner *= p->M[j];
   PassPlan pp;
-  int rc = plan_pass(p, axis, outer, inner, f64, &pp);
+  int rc = plan_pass(p, mode, axis, outer, inner, f64, &pp);
   if (rc) return rc;
   PassParams& P = pp.P;
   P.in = in;
@@ -330,10 +344,35 @@ int apply_launch(fem_fft_plan p, const ApplyParams& P, cudaStream_t s) {
     if (P.base) bytes += elems * 8.0;
     if (P.addend) bytes += elems * 8.0;
   }
-  const double n1 = P.n + 1;
-  const double flops = elems * P.nterm * 2.0 * n1 * n1 / P.n;
+  // executed float64 flops of the even/odd element products (FMA = 2):
+  // per element and term 2 R (P+1) + 2 R P (half-size products), 3 P + 1
+  // (split), 2 R (combine) and 4 R for the constant response of mass terms
+  const int n = P.n, R = n / 2 + 1, Pp = (n + 1) / 2;
+  double per_elem = 0.0;
+  for (int t = 0; t < P.nterm; ++t) {
+    bool mass = false;
+    for (int r = 0; r <= n; ++r) mass |= P.rows1[t][r] != 0.0;
+    const int ns = (n % 2 == 0) ? Pp + 1 : Pp;
+    per_elem += 2.0 * R * ns + 2.0 * R * Pp + 3.0 * Pp + 2 + 2.0 * R + (mass ? 2.0 * R : 0.0);
+  }
+  const double flops = elems / n * per_elem;
   ProfScope scope(p, s, 3, bytes, flops);
   return launch_apply(P, s);
+}
+
+// Even/odd halves of a bisymmetric element matrix M ((n+1)^2) in the layout
+// of the apply kernel: Es' (R x (P+1)) then Ea' (R x P), R = n/2 + 1,
+// P = (n+1)/2, Es'[q][j] = (M[q][j] + M[q][n-j]) / 2 (j < n/2; column P: the
+// middle node M[q][n/2] for even n, else 0), Ea'[q][j] = (M[q][j] - M[q][n-j]) / 2.
+void pack_even_odd(const std::vector<double>& Mx, int n, double* out) {
+  const int n1 = n + 1, R = n / 2 + 1, P = (n + 1) / 2, SP = P + 1;
+  for (int q = 0; q < R; ++q) {
+    for (int j = 0; j < P; ++j) {
+      out[q * SP + j] = 0.5 * (Mx[q * n1 + j] + Mx[q * n1 + (n - j)]);
+      out[R * SP + q * P + j] = 0.5 * (Mx[q * n1 + j] - Mx[q * n1 + (n - j)]);
+    }
+    out[q * SP + P] = (n % 2 == 0) ? Mx[q * n1 + n / 2] : 0.0;
+  }
 }
 
 // Term t of an apply launch: matrix alpha E + beta E2 where E, E2 are the
@@ -341,7 +380,9 @@ int apply_launch(fem_fft_plan p, const ApplyParams& P, cudaStream_t s) {
 // are alpha (E 1) + beta (E2 1) with A 1 = 0 and C 1 = Crow.
 void set_mat(ApplyParams& A, int t, const std::vector<double>& E, double alpha, const std::vector<double>* E2,
              double beta, int n1, const std::vector<double>& Aref, const std::vector<double>& Crow) {
-  for (int i = 0; i < n1 * n1; ++i) A.mats[t][i] = alpha * E[i] + (E2 ? beta * (*E2)[i] : 0.0);
+  std::vector<double> M(n1 * n1);
+  for (int i = 0; i < n1 * n1; ++i) M[i] = alpha * E[i] + (E2 ? beta * (*E2)[i] : 0.0);
+  pack_even_odd(M, n1 - 1, A.mats[t]);
   const bool e_is_mass = &E != &Aref;
   for (int r = 0; r < n1; ++r) {
     double v = e_is_mass ? alpha * Crow[r] : 0.0;

@@ -16,6 +16,7 @@
 // One thread computes the outputs of one element for all outputs of the
 // launch; inputs are read through the read-only cache (along strided axes the
 // threads of a warp cover consecutive positions of the contiguous axis).
+// Every entry of the element matrices is applied in the even/odd form below.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -52,93 +53,157 @@ __device__ void block_accumulate(double (&v)[NV], double* dst) {
   }
 }
 
-// One thread per (pencil position, element e): it produces the n outputs
-// owned by element e (its interior nodes and its right vertex).  Every element
-// product is evaluated in difference form, E u_e = E (u_e - u_e[0] 1) +
-// u_e[0] (E 1) with the EXACT row sums E 1: the stiffness rows annihilate
-// constants (Section 2, A (1..1)^T = 0), so the float64 products involve the
-// differences of neighbouring nodal values instead of the values themselves,
-// and the rounding of the entries of A (whose float64 row sums are ~1e-14,
-// not 0) cannot act as a spurious zeroth-order term 4 h^-2 (A 1) u, which
-// would shift the solution by ~6e-9 relative at K = 1024, n = 9.  For smooth u this removes
-// most of the cancellation of 4 h^-2 calA u (terms ~h^-2 |u|, result ~|u|),
-// which otherwise puts a rounding floor of ~1e-8 under the refined solution at
-// K = 1024, n = 9.
+// Even/odd element products.  A and C are bisymmetric (Section 2), so with
+// the centre reference ub = (u_0 + u_n)/2 and d = u_e - ub 1 the product
+// y = E d splits into half-size products of the symmetric sums
+// s_q = d_q + d_{n-q} and the antisymmetric differences a_q = u_q - u_{n-q}:
+//   y_q = Es'[q] . s + Ea'[q] . a,   y_{n-q} = Es'[q] . s - Ea'[q] . a   (q <= n/2),
+// with Es'[q][j] = (E[q][j] + E[q][n-j]) / 2, Ea'[q][j] = (E[q][j] - E[q][n-j]) / 2
+// (for even n the middle node enters Es' with E[q][n/2]).  The constant part
+// is added back with the exact row sums: E u_e = E d + ub (E 1), and
+// A 1 = 0 exactly (Section 2), so a stiffness term never multiplies the nodal
+// values themselves -- for smooth u the sums s are O(h^2 u'') and the
+// differences a are O(h u'), which keeps the float64 rounding of
+// 4 h^-2 calA u far below the refinement target.  (Rounded A has row sums
+// ~1e-14, not 0; using them would act as a spurious zeroth-order term and shift
+// the refined solution by ~6e-9 at K = 1024, n = 9.)
+//
+// Layout of mats[t]: Es' (R x (P+1), the last column is the middle node of
+// even n) followed by Ea' (R x P), R = n/2 + 1 rows q = 0..n/2, P = (n+1)/2
+// pairs j < n/2.
+//
+// A block covers TW consecutive positions of the contiguous axis (w) times
+// TE consecutive elements (TW * TE = kApplyThreads).  Each thread forms all
+// n+1 local rows of its element; the vertex between elements e and e+1 adds
+// row n of e and row 0 of e+1, exchanged through shared memory (the last
+// element row of a tile recomputes its neighbour's row 0).
+template <int NORD>
+struct EO {
+  static constexpr int N1 = NORD + 1;
+  static constexpr int R = NORD / 2 + 1;
+  static constexpr int P = (NORD + 1) / 2;
+  static constexpr int SP = P + 1;     // columns of Es'
+};
+
+template <int NORD>
+__device__ __forceinline__ void load_elem(const double* x, long long line, long long inner, int e, int M,
+                                          double (&u)[NORD + 1]) {
+#pragma unroll
+  for (int q = 0; q <= NORD; ++q) {
+    const int g = NORD * e + q - 1;
+    u[q] = (g >= 0 && g < M) ? __ldg(&x[line + (long long)g * inner]) : 0.0;
+  }
+}
+
+// y = E u for one element (all n+1 rows, or only row 0 when ROW0_ONLY)
+template <int NORD, bool ROW0_ONLY>
+__device__ __forceinline__ void elem_product(const double* Es, const double* Ea, const double* E1, bool has_e1,
+                                             const double (&u)[NORD + 1], double (&y)[NORD + 1]) {
+  using C = EO<NORD>;
+  const double ub = 0.5 * (u[0] + u[NORD]);
+  double sv[C::P + 1], av[C::P];
+#pragma unroll
+  for (int j = 0; j < C::P; ++j) {
+    sv[j] = (u[j] + u[NORD - j]) - 2.0 * ub;
+    av[j] = u[j] - u[NORD - j];
+  }
+  sv[C::P] = (NORD % 2 == 0) ? u[NORD / 2] - ub : 0.0;
+  constexpr int NS = (NORD % 2 == 0) ? C::SP : C::P;   // the middle column exists for even n only
+#pragma unroll
+  for (int q = 0; q < C::R; ++q) {
+    if (ROW0_ONLY && q > 0) break;
+    double ts = 0.0, ta = 0.0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) ts = fma(Es[q * C::SP + j], sv[j], ts);
+#pragma unroll
+    for (int j = 0; j < C::P; ++j) ta = fma(Ea[q * C::P + j], av[j], ta);
+    if (has_e1) {
+      y[q] = fma(ub, E1[q], ts + ta);
+      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = fma(ub, E1[NORD - q], ts - ta);
+    } else {
+      y[q] = ts + ta;
+      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = ts - ta;
+    }
+  }
+}
+
 template <int NORD, int NOUT>
-__global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyParams P) {
-  constexpr int N1 = NORD + 1;
-  __shared__ double mats[kApplyMaxTerms][N1 * N1];
-  __shared__ double rows1[kApplyMaxTerms][N1];     // exact E (1..1)^T
+__global__ void __launch_bounds__(kApplyThreads, 2) apply_kernel(ApplyParams P, int TW) {
+  using C = EO<NORD>;
+  constexpr int N1 = C::N1;
+  __shared__ double es[kApplyMaxTerms][C::R * C::SP];
+  __shared__ double ea[kApplyMaxTerms][C::R * C::P];
+  __shared__ double e1[kApplyMaxTerms][N1];
+  __shared__ double row0[NOUT][kApplyThreads];
+  __shared__ int has1[kApplyMaxTerms];
   for (int t = 0; t < P.nterm; ++t) {
-    for (int j = threadIdx.x; j < N1 * N1; j += blockDim.x) mats[t][j] = P.mats[t][j];
-    for (int r = threadIdx.x; r < N1; r += blockDim.x) rows1[t][r] = P.rows1[t][r];
+    for (int j = threadIdx.x; j < C::R * C::SP; j += blockDim.x) es[t][j] = P.mats[t][j];
+    for (int j = threadIdx.x; j < C::R * C::P; j += blockDim.x) ea[t][j] = P.mats[t][C::R * C::SP + j];
+    for (int r = threadIdx.x; r < N1; r += blockDim.x) e1[t][r] = P.rows1[t][r];
+    if (threadIdx.x == 0) {
+      int h = 0;
+      for (int r = 0; r < N1; ++r) h |= P.rows1[t][r] != 0.0;
+      has1[t] = h;
+    }
   }
   __syncthreads();
 
   const int K = P.K;
-  const long long total = P.outer * (long long)K * P.inner;
-  const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double dotacc[kApplyMaxOut] = {0.0, 0.0, 0.0, 0.0};   // NOUT <= kApplyMaxOut
-  double rr = 0.0, bb = 0.0;
-  if (pos < total) {
-    const long long w = pos % P.inner;
-    const long long rest = pos / P.inner;
-    const int e = (int)(rest % K);
-    const long long o = rest / K;
-    const long long line = o * (long long)P.M * P.inner + w;   // offset of index 0 of this pencil
-    const bool has_node = e < K - 1;                           // right vertex is an unknown
-    double acc[NOUT][NORD];
+  const int TE = kApplyThreads / TW;
+  const long long wtiles = (P.inner + TW - 1) / TW;
+  const long long etiles = (K + TE - 1) / TE;
+  long long bx = blockIdx.x;
+  const long long et = bx % etiles;
+  bx /= etiles;
+  const long long wt = bx % wtiles;
+  const long long o = bx / wtiles;
+  const int tw = threadIdx.x % TW, te = threadIdx.x / TW;
+  const long long w = wt * TW + tw;
+  const int e = (int)(et * TE + te);
+  const bool valid = w < P.inner && e < K;
+  const long long line = o * (long long)P.M * P.inner + (valid ? w : 0);
+
+  double acc[NOUT][N1];
 #pragma unroll
-    for (int j = 0; j < NOUT; ++j)
+  for (int j = 0; j < NOUT; ++j)
 #pragma unroll
-      for (int r = 0; r < NORD; ++r) acc[j][r] = 0.0;
+    for (int q = 0; q < N1; ++q) acc[j][q] = 0.0;
+  if (valid) {
     for (int t = 0; t < P.nterm; ++t) {
-      const double* x = P.in[P.t_src[t]];
-      const double* E = mats[t];
-      const double* E1 = rows1[t];
-      double ue[N1], un[N1];
-#pragma unroll
-      for (int q = 0; q <= NORD; ++q) {
-        int g = NORD * e + q - 1;
-        ue[q] = (g >= 0 && g < P.M) ? __ldg(&x[line + (long long)g * P.inner]) : 0.0;
-      }
-      if (has_node) {
-#pragma unroll
-        for (int q = 0; q <= NORD; ++q) {
-          int g = NORD * (e + 1) + q - 1;
-          un[q] = (g < P.M) ? __ldg(&x[line + (long long)g * P.inner]) : 0.0;
-        }
-      }
-      const double u0 = ue[0], v0 = un[0];
-#pragma unroll
-      for (int q = 1; q <= NORD; ++q) {
-        ue[q] -= u0;
-        if (has_node) un[q] -= v0;
-      }
-      double y[NORD];
-#pragma unroll
-      for (int s = 0; s < NORD - 1; ++s) {        // interior node s+1 of element e
-        double v = u0 * E1[s + 1];
-#pragma unroll
-        for (int q = 1; q <= NORD; ++q) v = fma(E[(s + 1) * N1 + q], ue[q], v);
-        y[s] = v;
-      }
-      if (has_node) {                              // vertex: row n of e + row 0 of e+1
-        double v = u0 * E1[NORD] + v0 * E1[0];
-#pragma unroll
-        for (int q = 1; q <= NORD; ++q) v = fma(E[NORD * N1 + q], ue[q], v);
-#pragma unroll
-        for (int q = 1; q <= NORD; ++q) v = fma(E[q], un[q], v);
-        y[NORD - 1] = v;
-      } else {
-        y[NORD - 1] = 0.0;
-      }
+      double u[N1], y[N1];
+      load_elem<NORD>(P.in[P.t_src[t]], line, P.inner, e, P.M, u);
+      elem_product<NORD, false>(es[t], ea[t], e1[t], has1[t], u, y);
       const int d = P.t_dst[t];
 #pragma unroll
       for (int j = 0; j < NOUT; ++j)
         if (j == d)
 #pragma unroll
-          for (int r = 0; r < NORD; ++r) acc[j][r] += y[r];
+          for (int q = 0; q < N1; ++q) acc[j][q] += y[q];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NOUT; ++j) row0[j][threadIdx.x] = acc[j][0];
+  __syncthreads();
+
+  double dotacc[kApplyMaxOut] = {0.0, 0.0, 0.0, 0.0};
+  double rr = 0.0, bb = 0.0;
+  if (valid) {
+    const bool has_node = e < K - 1;
+    if (has_node) {
+      if (te + 1 < TE) {
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) acc[j][NORD] += row0[j][threadIdx.x + TW];
+      } else {
+        for (int t = 0; t < P.nterm; ++t) {
+          double u[N1], y[N1];
+          load_elem<NORD>(P.in[P.t_src[t]], line, P.inner, e + 1, P.M, u);
+          elem_product<NORD, true>(es[t], ea[t], e1[t], has1[t], u, y);
+          const int d = P.t_dst[t];
+#pragma unroll
+          for (int j = 0; j < NOUT; ++j)
+            if (j == d) acc[j][NORD] += y[0];
+        }
+      }
     }
     const int nrow = has_node ? NORD : NORD - 1;
 #pragma unroll
@@ -148,12 +213,12 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyParams P) {
       if (P.dotv) {
         const double lv = __ldg(&P.dotv[off]);
 #pragma unroll
-        for (int j = 0; j < NOUT; ++j) dotacc[j] = fma(acc[j][r], lv, dotacc[j]);
+        for (int j = 0; j < NOUT; ++j) dotacc[j] = fma(acc[j][r + 1], lv, dotacc[j]);
       } else {
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) {
           if (j < P.nout) {
-            double v = acc[j][r];
+            double v = acc[j][r + 1];
             if (j == 0 && P.addend) v += P.addend[off];
             if (j == 0 && P.base) {
               double b = __ldg(&P.base[off]);
@@ -177,15 +242,17 @@ __global__ void __launch_bounds__(kApplyThreads) apply_kernel(ApplyParams P) {
 }
 
 int launch_apply(const ApplyParams& P, cudaStream_t s) {
-  const long long total = P.outer * (long long)P.K * P.inner;
-  if (total <= 0) return 0;
-  const long long blocks = (total + kApplyThreads - 1) / kApplyThreads;
+  if (P.outer * (long long)P.K * P.inner <= 0) return 0;
+  int TW = 1;
+  while (TW * 2 <= 32 && TW * 2 <= P.inner) TW *= 2;
+  const int TE = kApplyThreads / TW;
+  const long long blocks = P.outer * ((P.inner + TW - 1) / TW) * ((P.K + TE - 1) / TE);
   switch (P.n) {
-#define FEMFFT_APPLY_CASE(NN)                                                  \
-  case NN:                                                                     \
-    if (P.nout <= 1) apply_kernel<NN, 1><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P); \
-    else if (P.nout <= 2) apply_kernel<NN, 2><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P); \
-    else apply_kernel<NN, 4><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P); \
+#define FEMFFT_APPLY_CASE(NN)                                                              \
+  case NN:                                                                                 \
+    if (P.nout <= 1) apply_kernel<NN, 1><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P, TW); \
+    else if (P.nout <= 2) apply_kernel<NN, 2><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P, TW); \
+    else apply_kernel<NN, 4><<<(unsigned)blocks, kApplyThreads, 0, s>>>(P, TW);            \
     break;
     FEMFFT_APPLY_CASE(1) FEMFFT_APPLY_CASE(2) FEMFFT_APPLY_CASE(3) FEMFFT_APPLY_CASE(4)
     FEMFFT_APPLY_CASE(5) FEMFFT_APPLY_CASE(6) FEMFFT_APPLY_CASE(7) FEMFFT_APPLY_CASE(8)

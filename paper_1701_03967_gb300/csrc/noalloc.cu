@@ -91,8 +91,17 @@ ApplyParams base_params(const Ops& o, int axis) {
 
 // term t: alpha * (A if stiff else C) + beta * C, with exact row sums
 void term(const Ops& o, ApplyParams& P, int t, bool stiff, double alpha, double beta, int src, int dst) {
-  const int n1 = o.n + 1;
-  for (int i = 0; i < n1 * n1; ++i) P.mats[t][i] = alpha * (stiff ? o.A[i] : o.C[i]) + beta * o.C[i];
+  const int n1 = o.n + 1, n = o.n, R = n / 2 + 1, Pp = (n + 1) / 2, SP = Pp + 1;
+  std::vector<double> M(n1 * n1);
+  for (int i = 0; i < n1 * n1; ++i) M[i] = alpha * (stiff ? o.A[i] : o.C[i]) + beta * o.C[i];
+  // even/odd halves (layout of the apply kernel)
+  for (int q = 0; q < R; ++q) {
+    for (int j = 0; j < Pp; ++j) {
+      P.mats[t][q * SP + j] = 0.5 * (M[q * n1 + j] + M[q * n1 + (n - j)]);
+      P.mats[t][R * SP + q * Pp + j] = 0.5 * (M[q * n1 + j] - M[q * n1 + (n - j)]);
+    }
+    P.mats[t][q * SP + Pp] = (n % 2 == 0) ? M[q * n1 + n / 2] : 0.0;
+  }
   for (int r = 0; r < n1; ++r) P.rows1[t][r] = (stiff ? 0.0 : alpha * o.Crow[r]) + beta * o.Crow[r];
   P.t_src[t] = src;
   P.t_dst[t] = dst;

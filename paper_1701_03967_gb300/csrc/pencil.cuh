@@ -78,8 +78,16 @@ constexpr int kPencilThreads = 512; // threads per CTA of the float pencil passe
 constexpr int kPencilThreads64 = 256; // threads per CTA of the double pencil passes
 template <typename T>
 __host__ __device__ constexpr int pencil_threads() { return sizeof(T) == 8 ? kPencilThreads64 : kPencilThreads; }
+// float forward/inverse passes: two resident CTAs per SM (64 registers per
+// thread) so that the load/store phase of one overlaps the shared-memory
+// phases of the other; the fused pass keeps one CTA with 128 registers
+// (measured faster: its map/FFT phases dominate and need the registers)
+constexpr int kPencilCtasPerSm = 2;
+template <typename T, int MODE>
+__host__ __device__ constexpr int pencil_min_blocks() { return (sizeof(T) == 8 || MODE == 2) ? 1 : kPencilCtasPerSm; }
 constexpr int kMaxW = 32;           // pencils per CTA (float)
-constexpr int kMaxW64 = 12;         // pencils per CTA (double)
+constexpr int kMaxW64 = 8;          // pencils per CTA (double)
+constexpr int kSmallW = 4;          // pencil bound of the small-tile kernel variants
 template <typename T>
 __host__ __device__ constexpr int max_w() { return sizeof(T) == 8 ? kMaxW64 : kMaxW; }
 
@@ -143,6 +151,11 @@ __device__ __forceinline__ void dft8(cpx<T>* u) {
   u[1] = o[0]; u[3] = o[1]; u[5] = o[2]; u[7] = o[3];
 }
 
+// Complex offset of chunk k within a pencil (chunks are Q complex values
+// long; Q is odd for odd n, which keeps the unit-stride passes conflict-free).
+__host__ __device__ __forceinline__ int cofs(int k, int Q) { return k * Q; }
+__host__ __device__ __forceinline__ int pencil_pitch_min(int K, int Q) { return cofs(K, Q); }
+
 // Reordering of Makhoul's DCT via FFT: position r of the FFT sequence holds
 // element 2r (r < K/2) or element 2(K-1-r)+1 (r >= K/2).
 __device__ __forceinline__ int makhoul_perm(int r, int K) {
@@ -156,8 +169,8 @@ __device__ __forceinline__ int makhoul_perm(int r, int K) {
 // R-point DFT and writes element (i - i mod prod) R + (i mod prod) + r prod.
 // Sequence elements are Q complex values apart.
 template <typename T, int R>
-__device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassParams& P, int Q, int tau,
-                                         int tps, int prod, bool perm_in, bool perm_out) {
+__device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassParams& P, const cpx<T>* tw, int Q,
+                                         int tau, int tps, int prod, bool perm_in, bool perm_out) {
   const int K = P.ax.K;
   const int T_ = K / R;
   const int nb = P.V / R;
@@ -172,7 +185,7 @@ __device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassPa
         for (int r = 0; r < R; ++r) {
           int idx = i + r * T_;
           int src = perm_in ? makhoul_perm(idx, K) : idx;
-          u[g * R + r] = base[src * Q];
+          u[g * R + r] = base[cofs(src, Q)];
         }
       }
     }
@@ -187,7 +200,7 @@ __device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassPa
         const int kk = i % prod;
         if (prod > 1) {
 #pragma unroll
-          for (int r = 1; r < R; ++r) u[g * R + r] = cmul(u[g * R + r], ld_cpx<T>(P.ax.tw, r * kk * stride));
+          for (int r = 1; r < R; ++r) u[g * R + r] = cmul(u[g * R + r], tw[r * kk * stride]);
         }
         if (R == 2) dft2(&u[g * R]);
         if (R == 3) dft3(&u[g * R]);
@@ -198,7 +211,7 @@ __device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassPa
         for (int r = 0; r < R; ++r) {
           int dst = j + r * prod;
           if (perm_out) dst = makhoul_perm(dst, K);
-          base[dst * Q] = u[g * R + r];
+          base[cofs(dst, Q)] = u[g * R + r];
         }
       }
     }
@@ -212,7 +225,8 @@ __device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassPa
 // reordering); perm_out: the last pass writes element makhoul_perm(idx)
 // (DCT-III output reordering).
 template <typename T>
-__device__ void fft_all(cpx<T>* sm, const PassParams& P, int nseq, int Q, bool perm_in, bool perm_out) {
+__device__ void fft_all(cpx<T>* sm, const PassParams& P, const cpx<T>* tw, int nseq, int Q, bool perm_in,
+                        bool perm_out) {
   const int K = P.ax.K;
   const int tps = K / P.V;                  // tasks per sequence
   const int spr = blockDim.x / tps;         // sequences per round (host: >= 1)
@@ -230,79 +244,133 @@ __device__ void fft_all(cpx<T>* sm, const PassParams& P, int nseq, int Q, bool p
     for (int ps = 0; ps < P.npass; ++ps) {
       const int R = P.radix[ps];
       const bool pin = perm_in && ps == 0, pout = perm_out && ps == P.npass - 1;
-      if (R == 8) fft_pass<T, 8>(base, active, P, Q, tau, tps, prod, pin, pout);
-      else if (R == 4) fft_pass<T, 4>(base, active, P, Q, tau, tps, prod, pin, pout);
-      else if (R == 3) fft_pass<T, 3>(base, active, P, Q, tau, tps, prod, pin, pout);
-      else fft_pass<T, 2>(base, active, P, Q, tau, tps, prod, pin, pout);
+      if (R == 8) fft_pass<T, 8>(base, active, P, tw, Q, tau, tps, prod, pin, pout);
+      else if (R == 4) fft_pass<T, 4>(base, active, P, tw, Q, tau, tps, prod, pin, pout);
+      else if (R == 3) fft_pass<T, 3>(base, active, P, tw, Q, tau, tps, prod, pin, pout);
+      else fft_pass<T, 2>(base, active, P, tw, Q, tau, tps, prod, pin, pout);
       prod *= R;
     }
   }
-}
-
-template <typename T>
-__device__ __forceinline__ T load_in(const PassParams& P, size_t off) {
-  if (P.in_f64) return T(reinterpret_cast<const double*>(P.in)[off]);
-  return T(reinterpret_cast<const float*>(P.in)[off]);
-}
-template <typename T>
-__device__ __forceinline__ void store_out(const PassParams& P, size_t off, T v) {
-  if (P.out_f64) {
-    double* o = reinterpret_cast<double*>(P.out);
-    o[off] = P.accum ? o[off] + double(v) : double(v);
-  } else {
-    float* o = reinterpret_cast<float*>(P.out);
-    o[off] = P.accum ? o[off] + float(v) : float(v);
-  }
-}
-
-// global offset of pencil p, element i of this CTA's tile, or -1 if absent
-__device__ __forceinline__ long long pencil_offset(const PassGeom& g, int p, int i) {
-  const long long tile = blockIdx.x;
-  if (g.inner == 1) {
-    long long o = tile * g.W + p;
-    if (o >= g.outer) return -1;
-    return o * g.M + i;
-  }
-  long long o = tile / g.tiles_inner;
-  long long w = (tile - o * g.tiles_inner) * g.W + p;
-  if (w >= g.inner) return -1;
-  return (o * g.M + i) * g.inner + w;
 }
 
 // fine index j (or spectral sigma+1) -> real offset within a pencil
 template <int NORD, int Q2>
 __device__ __forceinline__ int chunk_slot(int j) {
   int e = j / NORD;
-  return e * Q2 + (j - e * NORD);
+  return 2 * cofs(e, Q2 / 2) + (j - e * NORD);
 }
 
+// Global offset of element 0 of pencil p of this CTA (or -1 if the pencil
+// lies beyond the array); the element stride along the pencil is g.inner.
+__device__ __forceinline__ long long pencil_base(const PassGeom& g, int p) {
+  const long long tile = blockIdx.x;
+  if (g.inner == 1) {
+    long long o = tile * g.W + p;
+    return o < g.outer ? o * g.M : -1;
+  }
+  long long o = tile / g.tiles_inner;
+  long long w = (tile - o * g.tiles_inner) * g.W + p;
+  return w < g.inner ? o * g.M * g.inner + w : -1;
+}
+
+constexpr int kLoadBatch = 8;   // independent global accesses in flight per thread
+
+// Global -> shared: element i of pencil p goes to chunk slot map(i) (space)
+// or map(i+1) (spectral).  Contiguous pencils (inner == 1): each pencil is
+// swept by the whole block; strided pencils: the W pencils of an element row
+// are adjacent in memory, so thread t serves pencil t mod W (W is a power of
+// two dividing the block size).  Loads are issued kLoadBatch at a time.
 template <typename T, int NORD>
 __device__ void load_tile(T* smr, const PassParams& P, bool spectral) {
-  constexpr int Q = NORD / 2 + 1;
+  constexpr int Q2 = 2 * (NORD / 2 + 1);
   const PassGeom& g = P.g;
-  const int total = g.W * g.M;
-  for (int f = threadIdx.x; f < total; f += blockDim.x) {
-    int p, i;
-    if (g.inner == 1) { p = f / g.M; i = f - p * g.M; }
-    else { i = f / g.W; p = f - i * g.W; }
-    long long off = pencil_offset(g, p, i);
-    T v = off >= 0 ? load_in<T>(P, (size_t)off) : T(0);
-    smr[2 * p * P.pitch + chunk_slot<NORD, 2 * Q>(spectral ? i + 1 : i)] = v;
+  const int M = g.M;
+  const int sh = spectral ? 1 : 0;
+  if (g.inner == 1) {
+    for (int p = 0; p < g.W; ++p) {
+      const long long base = pencil_base(g, p);
+      T* dst = smr + 2 * p * P.pitch;
+      for (int i0 = threadIdx.x; i0 < M; i0 += kLoadBatch * blockDim.x) {
+        T v[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int i = i0 + u * blockDim.x;
+          v[u] = T(0);
+          if (i < M && base >= 0) {
+            if (P.in_f64) v[u] = T(__ldg(reinterpret_cast<const double*>(P.in) + base + i));
+            else v[u] = T(__ldg(reinterpret_cast<const float*>(P.in) + base + i));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int i = i0 + u * blockDim.x;
+          if (i < M) dst[chunk_slot<NORD, Q2>(i + sh)] = v[u];
+        }
+      }
+    }
+    return;
+  }
+  const int W = g.W;
+  const int p = threadIdx.x & (W - 1);
+  const int istep = blockDim.x / W;
+  const long long base = pencil_base(g, p);
+  const long long stride = g.inner;
+  T* dst = smr + 2 * p * P.pitch;
+  for (int i0 = threadIdx.x / W; i0 < M; i0 += kLoadBatch * istep) {
+    T v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int i = i0 + u * istep;
+      v[u] = T(0);
+      if (i < M && base >= 0) {
+        const long long off = base + (long long)i * stride;
+        if (P.in_f64) v[u] = T(__ldg(reinterpret_cast<const double*>(P.in) + off));
+        else v[u] = T(__ldg(reinterpret_cast<const float*>(P.in) + off));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int i = i0 + u * istep;
+      if (i < M) dst[chunk_slot<NORD, Q2>(i + sh)] = v[u];
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_one(const PassParams& P, long long off, T v) {
+  if (P.out_f64) {
+    double* o = reinterpret_cast<double*>(P.out) + off;
+    *o = P.accum ? *o + double(v) : double(v);
+  } else {
+    float* o = reinterpret_cast<float*>(P.out) + off;
+    *o = P.accum ? *o + float(v) : float(v);
   }
 }
 
 template <typename T, int NORD>
 __device__ void store_tile(const T* smr, const PassParams& P, bool spectral) {
-  constexpr int Q = NORD / 2 + 1;
+  constexpr int Q2 = 2 * (NORD / 2 + 1);
   const PassGeom& g = P.g;
-  const int total = g.W * g.M;
-  for (int f = threadIdx.x; f < total; f += blockDim.x) {
-    int p, i;
-    if (g.inner == 1) { p = f / g.M; i = f - p * g.M; }
-    else { i = f / g.W; p = f - i * g.W; }
-    long long off = pencil_offset(g, p, i);
-    if (off >= 0) store_out<T>(P, (size_t)off, smr[2 * p * P.pitch + chunk_slot<NORD, 2 * Q>(spectral ? i + 1 : i)]);
+  const int M = g.M;
+  const int sh = spectral ? 1 : 0;
+  if (g.inner == 1) {
+    for (int p = 0; p < g.W; ++p) {
+      const long long base = pencil_base(g, p);
+      if (base < 0) continue;
+      const T* src = smr + 2 * p * P.pitch;
+      for (int i = threadIdx.x; i < M; i += blockDim.x) store_one<T>(P, base + i, src[chunk_slot<NORD, Q2>(i + sh)]);
+    }
+    return;
   }
+  const int W = g.W;
+  const int p = threadIdx.x & (W - 1);
+  const int istep = blockDim.x / W;
+  const long long base = pencil_base(g, p);
+  if (base < 0) return;
+  const long long stride = g.inner;
+  const T* src = smr + 2 * p * P.pitch;
+  for (int i = threadIdx.x / W; i < M; i += istep)
+    store_one<T>(P, base + (long long)i * stride, src[chunk_slot<NORD, Q2>(i + sh)]);
 }
 
 // Build the Q packed complex sequences of every pencil in place:
@@ -321,7 +389,7 @@ __device__ void build_sequences(cpx<T>* sm, const PassParams& P) {
     if (c < nchunks) {
       int p = c / K, e = c - p * K;
       const T* smr = reinterpret_cast<const T*>(sm + p * P.pitch);
-      if (e > 0) xl[t] = smr[(e - 1) * 2 * Q + (NORD - 1)];
+      if (e > 0) xl[t] = smr[2 * cofs(e - 1, Q) + (NORD - 1)];
     }
   }
   __syncthreads();
@@ -330,7 +398,7 @@ __device__ void build_sequences(cpx<T>* sm, const PassParams& P) {
     int c = threadIdx.x + t * blockDim.x;
     if (c < nchunks) {
       int p = c / K, e = c - p * K;
-      T* smr = reinterpret_cast<T*>(sm + p * P.pitch) + e * 2 * Q;
+      T* smr = reinterpret_cast<T*>(sm + p * P.pitch) + 2 * cofs(e, Q);
       T y[NORD];
 #pragma unroll
       for (int s = 0; s < NORD; ++s) y[s] = smr[s];
@@ -360,7 +428,7 @@ __device__ void reconstruct(cpx<T>* sm, const PassParams& P) {
   const int nchunks = P.g.W * K;
   for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
     int p = c / K, e = c - p * K;
-    cpx<T>* ch = sm + p * P.pitch + e * Q;
+    cpx<T>* ch = sm + p * P.pitch + cofs(e, Q);
     cpx<T> x[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) x[q] = ch[q];
@@ -412,7 +480,7 @@ __device__ __forceinline__ T pencil_den_base(const PassParams& P, int p) {
 // (Re A + Re B, Re A - Re B).  Chunk 0 already holds (S_q(K), C_q(0)) =
 // (Re V_0, Im V_0).
 template <typename T, int NORD>
-__device__ void post_twiddle(cpx<T>* sm, const PassParams& P) {
+__device__ void post_twiddle(cpx<T>* sm, const PassParams& P, const cpx<T>* rot) {
   constexpr int Q = NORD / 2 + 1;
   const int K = P.ax.K;
   const int npairs = K / 2;
@@ -424,11 +492,11 @@ __device__ void post_twiddle(cpx<T>* sm, const PassParams& P) {
     const int p = r / npairs;
     cpx<T>* pen = sm + p * P.pitch;
     const int kk = K - k;
-    const cpx<T> rk = ld_cpx<T>(P.ax.rot, k);
-    const cpx<T> A = cmul(rk, pen[k * Q + q]);
-    const cpx<T> B = cmul(cpx<T>{rk.re, -rk.im}, pen[kk * Q + q]);
-    pen[k * Q + q] = {B.im - A.im, A.im + B.im};
-    if (kk != k) pen[kk * Q + q] = {A.re + B.re, A.re - B.re};
+    const cpx<T> rk = rot[k];
+    const cpx<T> A = cmul(rk, pen[cofs(k, Q) + q]);
+    const cpx<T> B = cmul(cpx<T>{rk.re, -rk.im}, pen[cofs(kk, Q) + q]);
+    pen[cofs(k, Q) + q] = {B.im - A.im, A.im + B.im};
+    if (kk != k) pen[cofs(kk, Q) + q] = {A.re + B.re, A.re - B.re};
   }
   __syncthreads();
 }
@@ -438,7 +506,26 @@ __device__ void post_twiddle(cpx<T>* sm, const PassParams& P) {
 // by the spectral denominator.  One thread per (k, l) loads the map row once
 // (coalesced) and applies it to all W pencils.  Rounds cover whole
 // frequencies so that every chunk is read completely before it is rewritten.
-template <typename T, int NORD, bool DIVIDE>
+// Division by a spectral denominator.  float64: Newton-Raphson reciprocal
+// (two steps from the float32 reciprocal, relative error ~2^-96 before the
+// final rounding), far cheaper than a float64 division on this GPU.
+__device__ __forceinline__ float divide_by(float x, float d) { return x / d; }
+__device__ __forceinline__ double divide_by(double x, double d) {
+  double r = double(__frcp_rn(float(d)));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  return x * r;
+}
+
+// Per-frequency forward maps (Theorem 2, item 2): coefficient (k, l) =
+// F_k[l] . (chunk k slots), for every pencil of the CTA; optionally divided
+// by the spectral denominator.  One thread per (k, l) loads the map row once
+// (coalesced) and applies it to all W pencils; the next round's rows are
+// prefetched while the current round computes.  Rounds cover whole
+// frequencies so that every chunk is read completely before it is rewritten.
+template <typename T, int NORD, bool DIVIDE, int WM>
 __device__ void forward_map(cpx<T>* sm, const PassParams& P, const T* base) {
   constexpr int Q2 = 2 * (NORD / 2 + 1);
   const int K = P.ax.K;
@@ -447,25 +534,30 @@ __device__ void forward_map(cpx<T>* sm, const PassParams& P, const T* base) {
   const T* mu = reinterpret_cast<const T*>(P.ax.mu);
   const int kpr = blockDim.x / NORD;
   const int kl = threadIdx.x / NORD, l = threadIdx.x - kl * NORD;
+  T f[Q2], fn[Q2];
+  T m = T(0), mn = T(0);
+  auto fetch = [&](int k, T* dst, T& md) {
+    if (kl < kpr && k < K) {
+#pragma unroll
+      for (int j = 0; j < Q2; ++j) dst[j] = __ldg(&F[((size_t)k * NORD + l) * Q2 + j]);
+      if (DIVIDE && !(k == 0 && l == NORD - 1)) md = __ldg(&mu[(k == 0) ? l : NORD * k - 1 + l]);
+    }
+  };
+  fetch(kl, f, m);
   for (int k0 = 0; k0 < K; k0 += kpr) {
     const int k = k0 + kl;
     const bool act = kl < kpr && k < K && !(k == 0 && l == NORD - 1);
-    constexpr int WM = max_w<T>();
+    fetch(k + kpr, fn, mn);
     T out[WM];
     if (act) {
-      T f[Q2];
-#pragma unroll
-      for (int j = 0; j < Q2; ++j) f[j] = __ldg(&F[((size_t)k * NORD + l) * Q2 + j]);
-      const int sigma = (k == 0) ? l : NORD * k - 1 + l;
-      const T m = DIVIDE ? __ldg(&mu[sigma]) : T(0);
 #pragma unroll
       for (int p = 0; p < WM; ++p) {
         if (p < W) {
-          const T* ch = reinterpret_cast<const T*>(sm + p * P.pitch) + k * Q2;
+          const T* ch = reinterpret_cast<const T*>(sm + p * P.pitch) + 2 * cofs(k, Q2 / 2);
           T acc = T(0);
 #pragma unroll
           for (int j = 0; j < Q2; ++j) acc += f[j] * ch[j];
-          if (DIVIDE) acc = acc / (base[p] + m);
+          if (DIVIDE) acc = divide_by(acc, base[p] + m);
           out[p] = acc;
         }
       }
@@ -475,9 +567,12 @@ __device__ void forward_map(cpx<T>* sm, const PassParams& P, const T* base) {
       const int slot = (k == 0) ? l + 1 : l;
 #pragma unroll
       for (int p = 0; p < WM; ++p)
-        if (p < W) reinterpret_cast<T*>(sm + p * P.pitch)[k * Q2 + slot] = out[p];
+        if (p < W) reinterpret_cast<T*>(sm + p * P.pitch)[2 * cofs(k, Q2 / 2) + slot] = out[p];
     }
     __syncthreads();
+#pragma unroll
+    for (int j = 0; j < Q2; ++j) f[j] = fn[j];
+    m = mn;
   }
 }
 
@@ -485,7 +580,7 @@ __device__ void forward_map(cpx<T>* sm, const PassParams& P, const T* base) {
 // w_k, where w_k are the n spectral values of frequency k (slots 0..n-1, or
 // 1..n-1 for the bubble modes of k = 0).  Slot 2q receives half the sine
 // coefficient a_q, slot 2q+1 half the cosine coefficient b_q of sequence q.
-template <typename T, int NORD>
+template <typename T, int NORD, int WM>
 __device__ void inverse_map(cpx<T>* sm, const PassParams& P) {
   constexpr int Q2 = 2 * (NORD / 2 + 1);
   const int K = P.ax.K;
@@ -493,21 +588,26 @@ __device__ void inverse_map(cpx<T>* sm, const PassParams& P) {
   const T* I = reinterpret_cast<const T*>(P.ax.inv);
   const int kpr = blockDim.x / Q2;
   const int kl = threadIdx.x / Q2, j = threadIdx.x - kl * Q2;
+  T f[NORD], fn[NORD];
+  auto fetch = [&](int k, T* dst) {
+    if (kl < kpr && k < K) {
+#pragma unroll
+      for (int l = 0; l < NORD; ++l) dst[l] = __ldg(&I[((size_t)k * Q2 + j) * NORD + l]);
+    }
+  };
+  fetch(kl, f);
   for (int k0 = 0; k0 < K; k0 += kpr) {
     const int k = k0 + kl;
     const bool act = kl < kpr && k < K;
-    constexpr int WM = max_w<T>();
+    fetch(k + kpr, fn);
     T out[WM];
     if (act) {
-      T f[NORD];
-#pragma unroll
-      for (int l = 0; l < NORD; ++l) f[l] = __ldg(&I[((size_t)k * Q2 + j) * NORD + l]);
       const int off = (k == 0) ? 1 : 0;
       const int nl = (k == 0) ? NORD - 1 : NORD;
 #pragma unroll
       for (int p = 0; p < WM; ++p) {
         if (p < W) {
-          const T* ch = reinterpret_cast<const T*>(sm + p * P.pitch) + k * Q2 + off;
+          const T* ch = reinterpret_cast<const T*>(sm + p * P.pitch) + 2 * cofs(k, Q2 / 2) + off;
           T acc = T(0);
 #pragma unroll
           for (int l = 0; l < NORD; ++l)
@@ -520,9 +620,11 @@ __device__ void inverse_map(cpx<T>* sm, const PassParams& P) {
     if (act) {
 #pragma unroll
       for (int p = 0; p < WM; ++p)
-        if (p < W) reinterpret_cast<T*>(sm + p * P.pitch)[k * Q2 + j] = out[p];
+        if (p < W) reinterpret_cast<T*>(sm + p * P.pitch)[2 * cofs(k, Q2 / 2) + j] = out[p];
     }
     __syncthreads();
+#pragma unroll
+    for (int l = 0; l < NORD; ++l) f[l] = fn[l];
   }
 }
 
@@ -533,7 +635,7 @@ __device__ void inverse_map(cpx<T>* sm, const PassParams& P) {
 // exp(-i phi_{K-k}) = -i exp(+i phi_k).  Chunk 0 already holds
 // H_0 = a_q(K) + i b_q(0).
 template <typename T, int NORD>
-__device__ void pre_twiddle(cpx<T>* sm, const PassParams& P) {
+__device__ void pre_twiddle(cpx<T>* sm, const PassParams& P, const cpx<T>* rot) {
   constexpr int Q = NORD / 2 + 1;
   const int K = P.ax.K;
   const int npairs = K / 2;
@@ -545,22 +647,30 @@ __device__ void pre_twiddle(cpx<T>* sm, const PassParams& P) {
     const int p = r / npairs;
     cpx<T>* pen = sm + p * P.pitch;
     const int kk = K - k;
-    const cpx<T> rk = ld_cpx<T>(P.ax.rot, k);
-    const cpx<T> vk = pen[k * Q + q];      // (a(k), b(k))
-    const cpx<T> vkk = pen[kk * Q + q];    // (a(K-k), b(K-k))
-    pen[k * Q + q] = cmul(rk, cpx<T>{vkk.re - vkk.im, vk.re + vk.im});
-    if (kk != k) pen[kk * Q + q] = cmul(cmi(cpx<T>{rk.re, -rk.im}), cpx<T>{vk.re - vk.im, vkk.re + vkk.im});
+    const cpx<T> rk = rot[k];
+    const cpx<T> vk = pen[cofs(k, Q) + q];      // (a(k), b(k))
+    const cpx<T> vkk = pen[cofs(kk, Q) + q];    // (a(K-k), b(K-k))
+    pen[cofs(k, Q) + q] = cmul(rk, cpx<T>{vkk.re - vkk.im, vk.re + vk.im});
+    if (kk != k) pen[cofs(kk, Q) + q] = cmul(cmi(cpx<T>{rk.re, -rk.im}), cpx<T>{vk.re - vk.im, vkk.re + vkk.im});
   }
   __syncthreads();
 }
 
-template <typename T, int NORD, int MODE>
-__global__ void __launch_bounds__(pencil_threads<T>(), 1) pencil_pass_kernel(PassParams P) {
+template <typename T, int NORD, int MODE, int WM>
+__global__ void __launch_bounds__(pencil_threads<T>(), (pencil_min_blocks<T, MODE>())) pencil_pass_kernel(PassParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T base[kMaxW];
+  __shared__ T base[WM];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   T* smr = reinterpret_cast<T*>(smem_raw);
   constexpr int Q = NORD / 2 + 1;
+  const int K = P.ax.K;
+  // FFT twiddles and DCT rotations, staged after the pencils
+  cpx<T>* tw = sm + P.g.W * P.pitch;
+  cpx<T>* rot = tw + K;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    tw[i] = ld_cpx<T>(P.ax.tw, i);
+    rot[i] = ld_cpx<T>(P.ax.rot, i);
+  }
   if (MODE == MODE_FUSED && threadIdx.x < P.g.W) base[threadIdx.x] = pencil_den_base<T, NORD>(P, threadIdx.x);
   if (MODE == MODE_INV) {
     load_tile<T, NORD>(smr, P, true);
@@ -569,17 +679,17 @@ __global__ void __launch_bounds__(pencil_threads<T>(), 1) pencil_pass_kernel(Pas
     load_tile<T, NORD>(smr, P, false);
     __syncthreads();
     build_sequences<T, NORD>(sm, P);
-    fft_all<T>(sm, P, P.g.W * Q, Q, true, false);
-    post_twiddle<T, NORD>(sm, P);
-    forward_map<T, NORD, MODE == MODE_FUSED>(sm, P, base);
+    fft_all<T>(sm, P, tw, P.g.W * Q, Q, true, false);
+    post_twiddle<T, NORD>(sm, P, rot);
+    forward_map<T, NORD, MODE == MODE_FUSED, WM>(sm, P, base);
     if (MODE == MODE_FWD) {
       store_tile<T, NORD>(smr, P, true);
       return;
     }
   }
-  inverse_map<T, NORD>(sm, P);
-  pre_twiddle<T, NORD>(sm, P);
-  fft_all<T>(sm, P, P.g.W * Q, Q, false, true);
+  inverse_map<T, NORD, WM>(sm, P);
+  pre_twiddle<T, NORD>(sm, P, rot);
+  fft_all<T>(sm, P, tw, P.g.W * Q, Q, false, true);
   reconstruct<T, NORD>(sm, P);
   store_tile<T, NORD>(smr, P, false);
 }

@@ -5,9 +5,9 @@
 
 namespace femfft {
 
-template <typename T, int NORD, int MODE>
-static int launch_one(const PassParams& P, size_t smem, int threads, cudaStream_t s) {
-  auto kern = pencil_pass_kernel<T, NORD, MODE>;
+template <typename T, int NORD, int MODE, int WM>
+static int launch_wm(const PassParams& P, size_t smem, int threads, cudaStream_t s) {
+  auto kern = pencil_pass_kernel<T, NORD, MODE, WM>;
   static size_t configured = 0;   // max dynamic smem already enabled for this instantiation
   if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -16,6 +16,14 @@ static int launch_one(const PassParams& P, size_t smem, int threads, cudaStream_
   }
   kern<<<(unsigned)P.g.tiles, threads, smem, s>>>(P);
   return (int)cudaGetLastError();
+}
+
+// Small tiles (W <= kSmallW) use a variant whose per-thread pencil loops are
+// bounded by kSmallW at compile time.
+template <typename T, int NORD, int MODE>
+static int launch_one(const PassParams& P, size_t smem, int threads, cudaStream_t s) {
+  if (P.g.W <= kSmallW) return launch_wm<T, NORD, MODE, kSmallW>(P, smem, threads, s);
+  return launch_wm<T, NORD, MODE, max_w<T>()>(P, smem, threads, s);
 }
 
 template <typename T, int MODE>

@@ -135,8 +135,7 @@ static void reference_matrices_dd(int n, std::vector<dd>* A, std::vector<dd>* C)
       der[l * G + g] = dsum;
     }
   }
-  A->assign((n + 1) * (n + 1), dd(0.0));
-  C->assign((n + 1) * (n + 1), dd(0.0));
+  std::vector<dd> Araw((n + 1) * (n + 1)), Craw((n + 1) * (n + 1));
   for (int k = 0; k <= n; ++k)
     for (int l = 0; l <= n; ++l) {
       dd sa(0.0), sc(0.0);
@@ -144,8 +143,20 @@ static void reference_matrices_dd(int n, std::vector<dd>* A, std::vector<dd>* C)
         sa += wg[g] * der[k * G + g] * der[l * G + g];
         sc += wg[g] * val[k * G + g] * val[l * G + g];
       }
-      (*A)[k * (n + 1) + l] = sa;
-      (*C)[k * (n + 1) + l] = sc;
+      Araw[k * (n + 1) + l] = sa;
+      Craw[k * (n + 1) + l] = sc;
+    }
+  // A and C are symmetric and bisymmetric (Section 2); average the four
+  // equivalent entries so that the rounded matrices keep both symmetries
+  // exactly (the even/odd element products rely on it)
+  A->assign((n + 1) * (n + 1), dd(0.0));
+  C->assign((n + 1) * (n + 1), dd(0.0));
+  for (int k = 0; k <= n; ++k)
+    for (int l = 0; l <= n; ++l) {
+      const int i0 = k * (n + 1) + l, i1 = l * (n + 1) + k, i2 = (n - k) * (n + 1) + (n - l),
+                i3 = (n - l) * (n + 1) + (n - k);
+      (*A)[i0] = (Araw[i0] + Araw[i1] + Araw[i2] + Araw[i3]) * dd(0.25);
+      (*C)[i0] = (Craw[i0] + Craw[i1] + Craw[i2] + Craw[i3]) * dd(0.25);
     }
 }
 
