@@ -94,6 +94,15 @@ enum fem_fft_precision {
 int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, const double* h_X,
                         const double* h_a, double c, int precision, int64_t max_nrhs, void* stream);
 
+/*
+ * fem_fft_plan_set_coefficients -- replace a_i and c of an existing plan
+ * (Section 4 operator).  The 1D eigenpairs do not depend on them, so only the
+ * denominator tables a_i 4 h_i^-2 lambda are recomputed and re-uploaded;
+ * this is what differentiation with respect to a_i, c iterates on.
+ * Same validity rules as fem_fft_plan_create.  Synchronous on stream.
+ */
+int fem_fft_plan_set_coefficients(fem_fft_plan plan, const double* h_a, double c, void* stream);
+
 /* Frees the plan's device tables and workspace (synchronises its stream). */
 int fem_fft_plan_destroy(fem_fft_plan plan);
 

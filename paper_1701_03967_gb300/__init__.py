@@ -16,7 +16,7 @@ import ctypes
 from . import _lib
 from ._lib import FEM_FFT_FP64, FEM_FFT_MIXED, FemFftError  # noqa: F401
 
-__all__ = ["Plan", "FemFftError", "solve", "lib_path"]
+__all__ = ["Plan", "FemFftError", "solve", "lib_path", "fem_solve"]
 
 lib_path = _lib.LIB_PATH
 
@@ -120,7 +120,15 @@ class Plan:
                                               self._stream(stream)), "fem_fft_inverse")
         return w
 
-    def set_refinement(self, rtol=0.0, max_iter=1):
+    def set_coefficients(self, a, c, stream=None):
+        """Replace a_i and c (only the denominator tables are recomputed)."""
+        a = tuple(float(x) for x in a)
+        arr = (ctypes.c_double * self.N)(*a)
+        _lib.check(_lib.lib().fem_fft_plan_set_coefficients(self._h, arr, float(c), self._stream(stream)),
+                   "fem_fft_plan_set_coefficients")
+        self.a, self.c = a, float(c)
+
+    def set_refinement(self, rtol=0.0, max_iter=2):
         _lib.check(_lib.lib().fem_fft_set_refinement(self._h, float(rtol), int(max_iter)),
                    "fem_fft_set_refinement")
 
@@ -190,3 +198,9 @@ def solve(b, n, K, X=None, a=None, c=0.0, precision="fp64"):
         return p.solve(b)
     finally:
         p.close()
+
+
+def fem_solve(plan, f, a=None, c=None):
+    """Differentiable u = L(a, c)^{-1} f (see ``autograd.FemSolve``)."""
+    from .autograd import fem_solve as _fs
+    return _fs(plan, f, a, c)

@@ -40,6 +40,7 @@ def lib():
     sig = {
         "fem_fft_plan_create": ([ctypes.POINTER(vp), i32, i32, P64, PD, PD, f64, i32, i64, vp], i32),
         "fem_fft_plan_destroy": ([vp], i32),
+        "fem_fft_plan_set_coefficients": ([vp, PD, f64, vp], i32),
         "fem_fft_solve": ([vp, vp, vp, i64, vp], i32),
         "fem_fft_apply": ([vp, vp, vp, i64, vp], i32),
         "fem_fft_set_refinement": ([vp, f64, i32], i32),

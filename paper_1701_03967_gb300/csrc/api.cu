@@ -706,6 +706,32 @@ int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, con
   return FEM_FFT_OK;
 }
 
+int fem_fft_plan_set_coefficients(fem_fft_plan p, const double* h_a, double c, void* stream) {
+  if (!p || !h_a) return FEM_FFT_ERR_ARG;
+  double cmin = 0.0;
+  for (int i = 0; i < p->N; ++i) {
+    if (!(h_a[i] > 0.0) || !std::isfinite(h_a[i])) return FEM_FFT_ERR_ARG;
+    cmin -= M_PI * M_PI * h_a[i] / (p->X[i] * p->X[i]);
+  }
+  if (!std::isfinite(c) || !(c > cmin)) return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < p->N; ++i) {
+    AxisHost& ax = p->ax[i];
+    ax.a = h_a[i];
+    for (int m = 0; m < ax.M; ++m) ax.mu[m] = ax.a * ax.s * ax.lam[m];
+    std::vector<float> f32(ax.mu.begin(), ax.mu.end());
+    FEMFFT_CUDA(cudaMemcpyAsync(p->t64[i].mu, ax.mu.data(), ax.M * sizeof(double), cudaMemcpyHostToDevice, s),
+                "coefficients");
+    if (p->t32[i].mu)
+      FEMFFT_CUDA(cudaMemcpyAsync(p->t32[i].mu, f32.data(), ax.M * sizeof(float), cudaMemcpyHostToDevice, s),
+                  "coefficients");
+    FEMFFT_CUDA(cudaStreamSynchronize(s), "coefficients sync");
+    p->a[i] = h_a[i];
+  }
+  p->c = c;
+  return FEM_FFT_OK;
+}
+
 int fem_fft_set_refinement(fem_fft_plan p, double rtol, int max_iter) {
   if (!p || rtol < 0.0 || max_iter < 0) return FEM_FFT_ERR_ARG;
   p->rtol = rtol;
