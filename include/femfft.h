@@ -53,6 +53,7 @@ extern "C" {
 #endif
 
 typedef struct fem_fft_plan_s* fem_fft_plan;
+typedef struct fem_fft_batch_s* fem_fft_batch;
 
 enum fem_fft_status {
   FEM_FFT_OK = 0,
@@ -205,6 +206,94 @@ int fem_fft_profile_read(fem_fft_plan plan, int kind, int64_t* launches, double*
  */
 int fem_fft_apply_noalloc(int N, int n, const int64_t* h_K, const double* h_X, const double* h_a, double c,
                           const double* d_u, double* d_b, int64_t nrhs, void* stream);
+
+/*
+ * Batched solves (many problems of uneven N, n, K and right-hand-side counts
+ * replayed from one CUDA graph: per element order present, one
+ * dependency-driven kernel launch that runs every step of every problem of
+ * that order from a ticket-ordered work list).  Each problem
+ * is solved as fem_fft_solve would solve it with a mixed-precision plan:
+ * algorithm (a) of Section 4 in float32, then `steps` float64 residual
+ * refinement steps.  The batch is an execution schedule over existing plans;
+ * it owns no copy of their tables or workspaces.
+ *
+ * fem_fft_batch_create -- record the solve chains of nprob plans and build
+ * the work list.
+ *   plans    nprob distinct plans, each created with FEM_FFT_MIXED; they
+ *            must outlive the batch, and their own solves must not run
+ *            concurrently with the batch's (the workspaces are shared)
+ *   h_nrhs   right-hand sides per problem, 1 <= h_nrhs[p] <= the plan's max_nrhs
+ *   steps    refinement steps (0..16; 2 reaches float64 accuracy)
+ *   tune_cache  path of a JSON autotune cache (NULL: none).  Entries for this
+ *            GPU are read; new ones are written back.
+ *   tune     1: time candidate tile shapes (pencils per tile) and radix
+ *            schedules for every (n, K, contiguous/strided, pass) the batch
+ *            uses and is missing from the cache (a few seconds); 0: use the
+ *            cache, else the stand-alone passes' choices
+ *   stream   used for the tuning launches; the call synchronises it
+ * Returns FEM_FFT_ERR_ARG for a non-mixed or repeated plan or a pencil too
+ * large for the persistent kernel's shared memory.
+ */
+int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int nprob, const int64_t* h_nrhs,
+                         int steps, const char* tune_cache, int tune, void* stream);
+int fem_fft_batch_destroy(fem_fft_batch batch);
+
+/*
+ * fem_fft_batch_layout -- the packed layout of the batch's fields: problem p
+ * occupies float64 elements [h_offsets[p], h_offsets[p] + nrhs_p * DOF_p) of
+ * one buffer of *total_len elements, in the layout of fem_fft_solve
+ * ([nrhs][M_1..M_N], C order).  Also the number of steps (pencil passes and
+ * operator applies of all chains) and work items.  Any pointer may be NULL.
+ */
+int fem_fft_batch_layout(fem_fft_batch batch, int64_t* h_offsets, int64_t* total_len, int64_t* n_steps,
+                         int64_t* n_items);
+
+/*
+ * fem_fft_batch_solve -- d_u = L_p^-1 d_b for every problem p, both packed
+ * device buffers of total_len float64 (distinct; d_b is not modified).
+ * Asynchronous on stream: one graph launch (per element order, a counter
+ * reset and one kernel).  When d_b or d_u differ from the previous call the step table is
+ * rewritten first (this synchronises stream).  Device-side waits are bounded:
+ * check fem_fft_batch_status after the solve.
+ */
+int fem_fft_batch_solve(fem_fft_batch batch, const double* d_b, double* d_u, void* stream);
+
+/*
+ * fem_fft_batch_status -- synchronise stream and return the status of the
+ * last solve: FEM_FFT_OK, or FEM_FFT_ERR_TIMEOUT when a dependency wait gave
+ * up (the results are then incomplete; *h_step names the waiting step).
+ */
+int fem_fft_batch_status(fem_fft_batch batch, void* stream, int* h_status, int64_t* h_step);
+
+/*
+ * fem_fft_batch_tuning -- the tuned (n, K, strided, mode, W, V, split)
+ * entries of the passes the batch uses, 7 ints each in h_entries (mode: 0
+ * forward, 1 inverse, 2 fused pass; W pencils per tile; V FFT values per
+ * thread; split: the fused pass runs as forward-with-division + inverse), and
+ * microseconds per pencil in h_us.  Returns the entry count (at most
+ * max_entries are written).
+ */
+int fem_fft_batch_tuning(fem_fft_batch batch, int max_entries, int* h_entries, double* h_us);
+
+/* Time limit of one device-side dependency wait (default 2 s). */
+int fem_fft_batch_set_wait_limit(fem_fft_batch batch, double seconds);
+
+/*
+ * fem_fft_batch_hold_step -- test hook of the bounded waits: step `step`
+ * (which must have a predecessor) waits for one item more than its
+ * predecessor has, so that its waits run out; -1 restores the schedule.
+ * Takes effect at the next solve.
+ */
+int fem_fft_batch_hold_step(fem_fft_batch batch, int64_t step);
+
+/*
+ * fem_fft_batch_order -- the level order of the work list (host only): the
+ * steps of nprob chains of nsteps[p] steps, step 0 of every problem first
+ * (problems by decreasing `work`, which may be NULL), then step 1, and so on.
+ * Writes (problem, step) pairs to h_prob/h_step (sum of nsteps entries) and
+ * returns their count.
+ */
+int fem_fft_batch_order(int nprob, const int* nsteps, const double* work, int* h_prob, int* h_step);
 
 /* Static text for a status code; fem_fft_last_error: the last CUDA error
  * text recorded by this thread (empty if none). */

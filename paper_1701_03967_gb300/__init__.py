@@ -16,7 +16,7 @@ import ctypes
 from . import _lib
 from ._lib import FEM_FFT_FP64, FEM_FFT_MIXED, FemFftError  # noqa: F401
 
-__all__ = ["Plan", "FemFftError", "solve", "lib_path", "fem_solve"]
+__all__ = ["Plan", "Batch", "FemFftError", "solve", "lib_path", "fem_solve"]
 
 lib_path = _lib.LIB_PATH
 
@@ -188,6 +188,135 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many mixed-precision problems solved by one graph launch.
+
+    plans: distinct ``Plan`` objects created with precision="mixed" (kept
+    alive by the batch); nrhs: right-hand sides per problem (each <= the plan's
+    max_nrhs); steps: float64 refinement steps; tune: time tile shapes and
+    radix schedules for the passes the batch uses (missing from tune_cache);
+    tune_cache: JSON file of tuning results (read and updated).
+
+    Fields are packed: problem p occupies ``offsets[p] : offsets[p] +
+    nrhs[p] * plans[p].dof`` of one float64 CUDA tensor of ``total_len``
+    elements; ``pack`` / ``views`` convert."""
+
+    MODES = ("forward", "inverse", "fused")
+
+    def __init__(self, plans, nrhs=None, steps=2, tune=True, tune_cache=None, stream=None):
+        L = _lib.lib()
+        self.plans = list(plans)
+        self.nprob = len(self.plans)
+        self.nrhs = [1] * self.nprob if nrhs is None else [int(r) for r in nrhs]
+        if len(self.nrhs) != self.nprob:
+            raise ValueError("nrhs must have one entry per plan")
+        handles = (ctypes.c_void_p * self.nprob)(*[p._h for p in self.plans])
+        nr = (ctypes.c_int64 * self.nprob)(*self.nrhs)
+        h = ctypes.c_void_p()
+        cache = tune_cache.encode() if tune_cache else None
+        _lib.check(L.fem_fft_batch_create(ctypes.byref(h), handles, self.nprob, nr, int(steps), cache,
+                                          1 if tune else 0, Plan._stream(stream)), "fem_fft_batch_create")
+        self._h = h
+        offs = (ctypes.c_int64 * self.nprob)()
+        total, nsteps, nitems = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _lib.check(L.fem_fft_batch_layout(self._h, offs, ctypes.byref(total), ctypes.byref(nsteps),
+                                          ctypes.byref(nitems)), "fem_fft_batch_layout")
+        self.offsets = list(offs)
+        self.total_len = total.value
+        self.n_steps = nsteps.value
+        self.n_items = nitems.value
+
+    def solve(self, b, out=None, stream=None, check=False):
+        """u = L_p^{-1} b_p for every problem (packed float64 CUDA tensors)."""
+        torch = _torch()
+        for x, name in ((b, "b"),) + (((out, "out"),) if out is not None else ()):
+            if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or \
+                    not x.is_contiguous() or x.numel() != self.total_len:
+                raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of {self.total_len} elements")
+        u = torch.empty_like(b) if out is None else out
+        _lib.check(_lib.lib().fem_fft_batch_solve(self._h, b.data_ptr(), u.data_ptr(), Plan._stream(stream)),
+                   "fem_fft_batch_solve")
+        if check:
+            self.check(stream)
+        return u
+
+    def status(self, stream=None):
+        """(status code, step index of a timed-out wait or -1); synchronises."""
+        st, where = ctypes.c_int(), ctypes.c_int64()
+        _lib.lib().fem_fft_batch_status(self._h, Plan._stream(stream), ctypes.byref(st), ctypes.byref(where))
+        return st.value, where.value
+
+    def check(self, stream=None):
+        code, where = self.status(stream)
+        if code != 0:
+            raise FemFftError(code, f"batched solve (step {where})")
+
+    def views(self, flat):
+        """Per-problem views (nrhs_p, M_1..M_N) of a packed tensor."""
+        out = []
+        for p, pl in enumerate(self.plans):
+            n = self.nrhs[p] * pl.dof
+            out.append(flat[self.offsets[p]:self.offsets[p] + n].view((self.nrhs[p],) + tuple(pl.M)))
+        return out
+
+    def pack(self, fields):
+        """Packed CUDA float64 tensor from per-problem arrays (nrhs_p, M...)."""
+        torch = _torch()
+        flat = torch.empty(self.total_len, dtype=torch.float64, device="cuda")
+        for v, f in zip(self.views(flat), fields):
+            v.copy_(torch.as_tensor(f).reshape(v.shape))
+        return flat
+
+    def tuning(self):
+        """The tuned entries used by the batch: dicts with n, K, strided, mode,
+        W (pencils per tile), V (FFT values per thread), split, us_per_pencil."""
+        L = _lib.lib()
+        cnt = L.fem_fft_batch_tuning(self._h, 0, None, None)
+        ent = (ctypes.c_int * (7 * max(cnt, 1)))()
+        us = (ctypes.c_double * max(cnt, 1))()
+        L.fem_fft_batch_tuning(self._h, cnt, ent, us)
+        out = []
+        for i in range(cnt):
+            r = ent[7 * i:7 * i + 7]
+            out.append(dict(n=r[0], K=r[1], strided=r[2], mode=self.MODES[r[3]] if r[3] < 3 else r[3], W=r[4],
+                            V=r[5], split=r[6], us_per_pencil=us[i]))
+        return out
+
+    def set_wait_limit(self, seconds):
+        _lib.check(_lib.lib().fem_fft_batch_set_wait_limit(self._h, float(seconds)), "fem_fft_batch_set_wait_limit")
+
+    def hold_step(self, step):
+        """Test hook: make step `step` wait for an item count never reached
+        (-1 restores the schedule)."""
+        _lib.check(_lib.lib().fem_fft_batch_hold_step(self._h, int(step)), "fem_fft_batch_hold_step")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().fem_fft_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_order(nsteps, work=None):
+    """Level order of a work list (host only): list of (problem, step)."""
+    L = _lib.lib()
+    n = len(nsteps)
+    tot = sum(nsteps)
+    ns = (ctypes.c_int * max(n, 1))(*nsteps)
+    w = (ctypes.c_double * max(n, 1))(*work) if work is not None else None
+    op = (ctypes.c_int * max(tot, 1))()
+    os_ = (ctypes.c_int * max(tot, 1))()
+    k = L.fem_fft_batch_order(n, ns, w, op, os_)
+    if k < 0:
+        raise FemFftError(k, "fem_fft_batch_order")
+    return [(op[i], os_[i]) for i in range(k)]
 
 
 def solve(b, n, K, X=None, a=None, c=0.0, precision="fp64"):

@@ -54,6 +54,16 @@ def lib():
         "fem_fft_profile": ([vp, i32], i32),
         "fem_fft_profile_read": ([vp, i32, P64, PD, PD, PD], i32),
         "fem_fft_apply_noalloc": ([i32, i32, P64, PD, PD, f64, vp, vp, i64, vp], i32),
+        "fem_fft_batch_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i32, P64, i32, ctypes.c_char_p, i32, vp],
+                                 i32),
+        "fem_fft_batch_destroy": ([vp], i32),
+        "fem_fft_batch_layout": ([vp, P64, P64, P64, P64], i32),
+        "fem_fft_batch_solve": ([vp, vp, vp, vp], i32),
+        "fem_fft_batch_status": ([vp, vp, PI, P64], i32),
+        "fem_fft_batch_tuning": ([vp, i32, PI, PD], i32),
+        "fem_fft_batch_set_wait_limit": ([vp, f64], i32),
+        "fem_fft_batch_hold_step": ([vp, i64], i32),
+        "fem_fft_batch_order": ([i32, PI, PD, PI, PI], i32),
         "fem_fft_strerror": ([i32], ctypes.c_char_p),
         "fem_fft_last_error": ([], ctypes.c_char_p),
     }

@@ -10,10 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/femfft.h"
-#include "femfft_internal.h"
-#include "kernels.h"
-#include "pencil.cuh"
+#include "plan.h"
 
 using namespace femfft;
 
@@ -21,23 +18,11 @@ namespace {
 
 thread_local std::string g_last_error;
 
-int cuda_fail(cudaError_t e, const char* what) {
-  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
-  return FEM_FFT_ERR_CUDA;
-}
 #define FEMFFT_CUDA(call, what)                      \
   do {                                               \
     cudaError_t e_ = (cudaError_t)(call);            \
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
-
-struct DevTables {
-  void* tw = nullptr;
-  void* rot = nullptr;
-  void* fwd = nullptr;
-  void* inv = nullptr;
-  void* mu = nullptr;
-};
 
 bool valid_K(int64_t K) {
   if (K < 2 || K > (1 << 20)) return false;
@@ -47,70 +32,63 @@ bool valid_K(int64_t K) {
   return K == 1;
 }
 
-// FFT schedule for length K: values per thread V and radix sequence (every
-// radix divides V; V <= kMaxV).  Powers of two: radix 8 (then 4 or 2) with 8
-// values per thread; K with a factor 3: radix 3 with 12 (or 6) values.
-void fft_schedule(int K, bool f64, int* V, int* npass, int* radix) {
-  (void)f64;
+}  // namespace
+
+namespace femfft {
+
+void set_last_error(const std::string& what) { g_last_error = what; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return FEM_FFT_ERR_CUDA;
+}
+
+bool fft_schedule_v(int K, int V, int* npass, int* radix) {
+  if (K < 2 || V < 2 || V > kMaxV || K % V) return false;
   int a = 0, b = 0, k = K;
   while (k % 2 == 0) { k /= 2; ++a; }
   while (k % 3 == 0) { k /= 3; ++b; }
+  if (k != 1) return false;
   std::vector<int> r;
-  if (b > 0) {
-    for (int i = 0; i < b; ++i) r.push_back(3);
-    int aa = a;
-    if (aa >= 2) {
-      *V = 12;
-      while (aa >= 2) { r.push_back(4); aa -= 2; }
-      if (aa) r.push_back(2);
-    } else {
-      *V = 6;
-      if (aa) r.push_back(2);
-    }
-  } else if (a >= 3) {
-    *V = 8;
-    int aa = a;
-    while (aa >= 3) { r.push_back(8); aa -= 3; }
-    if (aa == 2) r.push_back(4);
-    if (aa == 1) r.push_back(2);
-  } else {
-    *V = K;          // K = 2 or 4
-    r.push_back(K);
+  if (b > 0 && V % 3) return false;
+  for (int i = 0; i < b; ++i) r.push_back(3);
+  while (a > 0) {
+    int e = (a >= 3 && V % 8 == 0) ? 3 : (a >= 2 && V % 4 == 0) ? 2 : 1;
+    if (V % 2) return false;
+    r.push_back(1 << e);
+    a -= e;
   }
+  if ((int)r.size() > kMaxRadixPasses) return false;
   *npass = (int)r.size();
   for (size_t i = 0; i < r.size(); ++i) radix[i] = r[i];
+  return true;
 }
 
-}  // namespace
+// Powers of two: radix 8 (then 4 or 2) with 8 values per thread; K with a
+// factor 3: radix 3, then 4s with 12 values per thread (6 when K has a single
+// factor 2).
+void fft_schedule(int K, int* V, int* npass, int* radix) {
+  int a = 0, k = K;
+  while (k % 2 == 0) { k /= 2; ++a; }
+  int v;
+  if (k > 1) v = a >= 2 ? 12 : 6;
+  else v = a >= 3 ? 8 : K;
+  *V = v;
+  fft_schedule_v(K, v, npass, radix);
+}
 
-struct fem_fft_plan_s {
-  int N = 0, n = 0, precision = 0;
-  int64_t K[kMaxN] = {0, 0, 0}, M[kMaxN] = {0, 0, 0};
-  double X[kMaxN] = {1, 1, 1}, a[kMaxN] = {1, 1, 1}, c = 0.0;
-  int64_t max_nrhs = 1, dof = 0;
-  AxisHost ax[kMaxN];
-  DevTables t64[kMaxN], t32[kMaxN];
-  std::vector<double> Aref, Cref;      // element matrices
-  std::vector<double> Crow;            // exact row sums of Cref (those of Aref are 0)
-  float* w32 = nullptr;                // mixed workspace [max_nrhs][dof]
-  double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};   // float64 temporaries
-  double* d_scalars = nullptr;         // device scalars (norms, dots)
-  double rtol = 0.0;
-  int max_iter = 2;
-  int last_iters = -1;
-  double last_rel = -1.0;
-  int smem_optin = 0;
-  std::vector<void*> allocs;
-  // kernel timing (fem_fft_profile)
-  struct ProfRec {
-    cudaEvent_t a, b;
-    int kind;
-    double bytes, flops;
-  };
-  bool profiling = false;
-  std::vector<ProfRec> prof;
-  std::vector<cudaEvent_t> event_pool;
-};
+void set_pass_tiles(PassParams& P, int W) {
+  P.g.W = W;
+  if (P.g.inner == 1) {
+    P.g.tiles_inner = 1;
+    P.g.tiles = (P.g.outer + W - 1) / W;
+  } else {
+    P.g.tiles_inner = (P.g.inner + W - 1) / W;
+    P.g.tiles = P.g.outer * P.g.tiles_inner;
+  }
+}
+
+}  // namespace femfft
 
 namespace {
 
@@ -195,7 +173,7 @@ int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inn
   const size_t csize = f64 ? 2 * sizeof(double) : 2 * sizeof(float);
   PassParams& P = pp->P;
   std::memset(&P, 0, sizeof(P));
-  fft_schedule(K, f64, &P.V, &P.npass, P.radix);
+  fft_schedule(K, &P.V, &P.npass, P.radix);
   int pitch = pencil_pitch_min(K, Q);   // chunks plus bank padding
   if (pitch % 2 == 0) pitch += 1;      // odd pitch spreads pencils over banks
   P.pitch = pitch;
@@ -244,14 +222,7 @@ int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inn
   P.g.outer = outer;
   P.g.inner = inner;
   P.g.M = M;
-  P.g.W = (int)W;
-  if (inner == 1) {
-    P.g.tiles_inner = 1;
-    P.g.tiles = (outer + W - 1) / W;
-  } else {
-    P.g.tiles_inner = (inner + W - 1) / W;
-    P.g.tiles = outer * P.g.tiles_inner;
-  }
+  set_pass_tiles(P, (int)W);
   const DevTables& d = f64 ? p->t64[axis] : p->t32[axis];
   P.ax.n = n;
   P.ax.K = K;
@@ -287,6 +258,16 @@ int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const
       P.dv.Mo[j - 1] = p->M[j];
       P.dv.mu_o[j - 1] = f64 ? p->t64[j].mu : p->t32[j].mu;
     }
+  }
+  if (p->rec) {
+    RecordedOp op;
+    std::memset(&op, 0, sizeof(op));
+    op.kind = 0;
+    op.mode = mode;
+    op.axis = axis;
+    op.pp = P;
+    p->rec->push_back(op);
+    return FEM_FFT_OK;
   }
   const double elems = (double)outer * P.g.M * inner;
   const double bytes = elems * ((in_f64 ? 8 : 4) + (out_f64 ? 8 : 4) * (accum ? 2 : 1));
@@ -333,6 +314,14 @@ int solve_chain(fem_fft_plan p, bool f64, const void* in, bool in_f64, void* wor
 // one row of an (n+1)x(n+1) element matrix (two at an element vertex), i.e.
 // 2 (n+1)^2 / n flops per position and term on average.
 int apply_launch(fem_fft_plan p, const ApplyParams& P, cudaStream_t s) {
+  if (p->rec) {
+    RecordedOp op;
+    std::memset(&op, 0, sizeof(op));
+    op.kind = 1;
+    op.ap = P;
+    p->rec->push_back(op);
+    return 0;
+  }
   const double elems = (double)P.outer * P.M * P.inner;
   int nin = 0;
   for (int i = 0; i < kApplyMaxIn; ++i) nin += P.in[i] != nullptr;
@@ -604,6 +593,24 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
 }
 
 }  // namespace
+
+namespace femfft {
+
+int record_mixed_solve(fem_fft_plan p, const double* b, double* u, long long nrhs, int steps,
+                       std::vector<RecordedOp>* ops) {
+  if (!p || !ops || p->precision != FEM_FFT_MIXED || nrhs < 1 || nrhs > p->max_nrhs || steps < 0)
+    return FEM_FFT_ERR_ARG;
+  p->rec = ops;
+  int rc = solve_chain(p, false, b, true, p->w32, u, false, nrhs, nullptr);
+  for (int it = 0; it < steps && !rc; ++it) {
+    rc = operator_chain(p, u, nrhs, 1, nullptr, b, p->w32, nullptr, nullptr);
+    if (!rc) rc = solve_chain(p, false, p->w32, false, p->w32, u, true, nrhs, nullptr);
+  }
+  p->rec = nullptr;
+  return rc;
+}
+
+}  // namespace femfft
 
 // ====================================================================== ABI
 

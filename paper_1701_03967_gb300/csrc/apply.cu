@@ -1,244 +1,15 @@
-// Matrix-free float64 application of the FEM operators along one axis.
-//
-// The 1D operators calA, calC of Section 2 are sums of the element blocks A, C
-// ((n+1) x (n+1), Lagrange basis on [-1, 1]) over the K elements, with the two
-// boundary vertices removed; their explicit rows are the node rows and the
-// interior rows of the 1D system in Section 2.  The N-D operator of Section 4
-// is a sum of Kronecker products of these, so L u (and the residual
-// b - L u, and the bilinear forms lam^T (dL/da_i) u) are evaluated as a short
-// chain of 1D applications along the axes, e.g. in 2D
-//     w = (a_1 s_1 calA_1 + c calC_1) u (axis 1), t = a_2 s_2 calA_2 u (axis 2),
-//     L u = calC_2 w + calC_1 t.
-// The stiffness factor of every term is applied to u itself and the mass
-// factors afterwards: a stiffness applied to an intermediate that carries
-// white rounding noise (such as calC_2 u) would amplify that noise by
-// ~4 h^-2 |A| and floor the refinement at ~6e-9 (2D, n = 9, K = 1024).
-// One thread computes the outputs of one element for all outputs of the
-// launch; inputs are read through the read-only cache (along strided axes the
-// threads of a warp cover consecutive positions of the contiguous axis).
-// Every entry of the element matrices is applied in the even/odd form below.
-#include <cuda_runtime.h>
-
-#include "kernels.h"
+// Stand-alone operator-apply kernel (one launch per 1D application); the
+// device code is in apply.cuh.
+#include "apply.cuh"
 
 namespace femfft {
 
-constexpr int kApplyThreads = 256;
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block sum of up to 4 values, then one atomicAdd per value.
-template <int NV>
-__device__ void block_accumulate(double (&v)[NV], double* dst) {
-  __shared__ double red[kApplyThreads / 32][NV];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
-  if (lane == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) red[wid][j] = v[j];
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      double x = lane < (int)(blockDim.x >> 5) ? red[lane][j] : 0.0;
-      x = warp_sum(x);
-      if (lane == 0 && x != 0.0) atomicAdd(&dst[j], x);
-    }
-  }
-}
-
-// Even/odd element products.  A and C are bisymmetric (Section 2), so with
-// the centre reference ub = (u_0 + u_n)/2 and d = u_e - ub 1 the product
-// y = E d splits into half-size products of the symmetric sums
-// s_q = d_q + d_{n-q} and the antisymmetric differences a_q = u_q - u_{n-q}:
-//   y_q = Es'[q] . s + Ea'[q] . a,   y_{n-q} = Es'[q] . s - Ea'[q] . a   (q <= n/2),
-// with Es'[q][j] = (E[q][j] + E[q][n-j]) / 2, Ea'[q][j] = (E[q][j] - E[q][n-j]) / 2
-// (for even n the middle node enters Es' with E[q][n/2]).  The constant part
-// is added back with the exact row sums: E u_e = E d + ub (E 1), and
-// A 1 = 0 exactly (Section 2), so a stiffness term never multiplies the nodal
-// values themselves -- for smooth u the sums s are O(h^2 u'') and the
-// differences a are O(h u'), which keeps the float64 rounding of
-// 4 h^-2 calA u far below the refinement target.  (Rounded A has row sums
-// ~1e-14, not 0; using them would act as a spurious zeroth-order term and shift
-// the refined solution by ~6e-9 at K = 1024, n = 9.)
-//
-// Layout of mats[t]: Es' (R x (P+1), the last column is the middle node of
-// even n) followed by Ea' (R x P), R = n/2 + 1 rows q = 0..n/2, P = (n+1)/2
-// pairs j < n/2.
-//
-// A block covers TW consecutive positions of the contiguous axis (w) times
-// TE consecutive elements (TW * TE = kApplyThreads).  Each thread forms all
-// n+1 local rows of its element; the vertex between elements e and e+1 adds
-// row n of e and row 0 of e+1, exchanged through shared memory (the last
-// element row of a tile recomputes its neighbour's row 0).
-template <int NORD>
-struct EO {
-  static constexpr int N1 = NORD + 1;
-  static constexpr int R = NORD / 2 + 1;
-  static constexpr int P = (NORD + 1) / 2;
-  static constexpr int SP = P + 1;     // columns of Es'
-};
-
-template <int NORD>
-__device__ __forceinline__ void load_elem(const double* x, long long line, long long inner, int e, int M,
-                                          double (&u)[NORD + 1]) {
-#pragma unroll
-  for (int q = 0; q <= NORD; ++q) {
-    const int g = NORD * e + q - 1;
-    u[q] = (g >= 0 && g < M) ? __ldg(&x[line + (long long)g * inner]) : 0.0;
-  }
-}
-
-// y = E u for one element (all n+1 rows, or only row 0 when ROW0_ONLY)
-template <int NORD, bool ROW0_ONLY>
-__device__ __forceinline__ void elem_product(const double* Es, const double* Ea, const double* E1, bool has_e1,
-                                             const double (&u)[NORD + 1], double (&y)[NORD + 1]) {
-  using C = EO<NORD>;
-  const double ub = 0.5 * (u[0] + u[NORD]);
-  double sv[C::P + 1], av[C::P];
-#pragma unroll
-  for (int j = 0; j < C::P; ++j) {
-    sv[j] = (u[j] + u[NORD - j]) - 2.0 * ub;
-    av[j] = u[j] - u[NORD - j];
-  }
-  sv[C::P] = (NORD % 2 == 0) ? u[NORD / 2] - ub : 0.0;
-  constexpr int NS = (NORD % 2 == 0) ? C::SP : C::P;   // the middle column exists for even n only
-#pragma unroll
-  for (int q = 0; q < C::R; ++q) {
-    if (ROW0_ONLY && q > 0) break;
-    double ts = 0.0, ta = 0.0;
-#pragma unroll
-    for (int j = 0; j < NS; ++j) ts = fma(Es[q * C::SP + j], sv[j], ts);
-#pragma unroll
-    for (int j = 0; j < C::P; ++j) ta = fma(Ea[q * C::P + j], av[j], ta);
-    if (has_e1) {
-      y[q] = fma(ub, E1[q], ts + ta);
-      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = fma(ub, E1[NORD - q], ts - ta);
-    } else {
-      y[q] = ts + ta;
-      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = ts - ta;
-    }
-  }
-}
-
 template <int NORD, int NOUT>
 __global__ void __launch_bounds__(kApplyThreads, 2) apply_kernel(ApplyParams P, int TW) {
-  using C = EO<NORD>;
-  constexpr int N1 = C::N1;
-  __shared__ double es[kApplyMaxTerms][C::R * C::SP];
-  __shared__ double ea[kApplyMaxTerms][C::R * C::P];
-  __shared__ double e1[kApplyMaxTerms][N1];
-  __shared__ double row0[NOUT][kApplyThreads];
-  __shared__ int has1[kApplyMaxTerms];
-  for (int t = 0; t < P.nterm; ++t) {
-    for (int j = threadIdx.x; j < C::R * C::SP; j += blockDim.x) es[t][j] = P.mats[t][j];
-    for (int j = threadIdx.x; j < C::R * C::P; j += blockDim.x) ea[t][j] = P.mats[t][C::R * C::SP + j];
-    for (int r = threadIdx.x; r < N1; r += blockDim.x) e1[t][r] = P.rows1[t][r];
-    if (threadIdx.x == 0) {
-      int h = 0;
-      for (int r = 0; r < N1; ++r) h |= P.rows1[t][r] != 0.0;
-      has1[t] = h;
-    }
-  }
+  __shared__ ApplySmem<NORD, NOUT, kApplyThreads> S;
+  apply_stage_mats<NORD, NOUT, kApplyThreads>(P, S);
   __syncthreads();
-
-  const int K = P.K;
-  const int TE = kApplyThreads / TW;
-  const long long wtiles = (P.inner + TW - 1) / TW;
-  const long long etiles = (K + TE - 1) / TE;
-  long long bx = blockIdx.x;
-  const long long et = bx % etiles;
-  bx /= etiles;
-  const long long wt = bx % wtiles;
-  const long long o = bx / wtiles;
-  const int tw = threadIdx.x % TW, te = threadIdx.x / TW;
-  const long long w = wt * TW + tw;
-  const int e = (int)(et * TE + te);
-  const bool valid = w < P.inner && e < K;
-  const long long line = o * (long long)P.M * P.inner + (valid ? w : 0);
-
-  double acc[NOUT][N1];
-#pragma unroll
-  for (int j = 0; j < NOUT; ++j)
-#pragma unroll
-    for (int q = 0; q < N1; ++q) acc[j][q] = 0.0;
-  if (valid) {
-    for (int t = 0; t < P.nterm; ++t) {
-      double u[N1], y[N1];
-      load_elem<NORD>(P.in[P.t_src[t]], line, P.inner, e, P.M, u);
-      elem_product<NORD, false>(es[t], ea[t], e1[t], has1[t], u, y);
-      const int d = P.t_dst[t];
-#pragma unroll
-      for (int j = 0; j < NOUT; ++j)
-        if (j == d)
-#pragma unroll
-          for (int q = 0; q < N1; ++q) acc[j][q] += y[q];
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < NOUT; ++j) row0[j][threadIdx.x] = acc[j][0];
-  __syncthreads();
-
-  double dotacc[kApplyMaxOut] = {0.0, 0.0, 0.0, 0.0};
-  double rr = 0.0, bb = 0.0;
-  if (valid) {
-    const bool has_node = e < K - 1;
-    if (has_node) {
-      if (te + 1 < TE) {
-#pragma unroll
-        for (int j = 0; j < NOUT; ++j) acc[j][NORD] += row0[j][threadIdx.x + TW];
-      } else {
-        for (int t = 0; t < P.nterm; ++t) {
-          double u[N1], y[N1];
-          load_elem<NORD>(P.in[P.t_src[t]], line, P.inner, e + 1, P.M, u);
-          elem_product<NORD, true>(es[t], ea[t], e1[t], has1[t], u, y);
-          const int d = P.t_dst[t];
-#pragma unroll
-          for (int j = 0; j < NOUT; ++j)
-            if (j == d) acc[j][NORD] += y[0];
-        }
-      }
-    }
-    const int nrow = has_node ? NORD : NORD - 1;
-#pragma unroll
-    for (int r = 0; r < NORD; ++r) {
-      if (r >= nrow) break;
-      const long long off = line + (long long)(NORD * e + r) * P.inner;
-      if (P.dotv) {
-        const double lv = __ldg(&P.dotv[off]);
-#pragma unroll
-        for (int j = 0; j < NOUT; ++j) dotacc[j] = fma(acc[j][r + 1], lv, dotacc[j]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < NOUT; ++j) {
-          if (j < P.nout) {
-            double v = acc[j][r + 1];
-            if (j == 0 && P.addend) v += P.addend[off];
-            if (j == 0 && P.base) {
-              double b = __ldg(&P.base[off]);
-              v = b - v;
-              rr = fma(v, v, rr);
-              bb = fma(b, b, bb);
-            }
-            if (j == 0 && P.out0_f32) P.out0_f32[off] = (float)v;
-            else P.out[j][off] = v;
-          }
-        }
-      }
-    }
-  }
-  if (P.dotv) {
-    block_accumulate<kApplyMaxOut>(dotacc, P.dots);
-  } else if (P.norms) {
-    double v2[2] = {rr, bb};
-    block_accumulate<2>(v2, P.norms);
-  }
+  apply_block<NORD, NOUT, kApplyThreads, true>(P, TW, blockIdx.x, S);
 }
 
 int launch_apply(const ApplyParams& P, cudaStream_t s) {

@@ -69,7 +69,9 @@ __device__ __forceinline__ cpx<T> ld_cpx(const void* base, int idx) {
   return {__ldg(p), __ldg(p + 1)};
 }
 
-enum PassMode { MODE_FWD = 0, MODE_INV = 1, MODE_FUSED = 2 };
+// MODE_FWD_DIV: the forward transform with the spectral division, stored in
+// spectral order (the fused pass split in two; used by the batched kernel).
+enum PassMode { MODE_FWD = 0, MODE_INV = 1, MODE_FUSED = 2, MODE_FWD_DIV = 3 };
 
 constexpr int kMaxV = 12;          // FFT values held per thread
 constexpr int kMaxChunkTasks = 8;  // chunks per thread in the sequence build
@@ -260,10 +262,9 @@ __device__ __forceinline__ int chunk_slot(int j) {
   return 2 * cofs(e, Q2 / 2) + (j - e * NORD);
 }
 
-// Global offset of element 0 of pencil p of this CTA (or -1 if the pencil
+// Global offset of element 0 of pencil p of tile `tile` (or -1 if the pencil
 // lies beyond the array); the element stride along the pencil is g.inner.
-__device__ __forceinline__ long long pencil_base(const PassGeom& g, int p) {
-  const long long tile = blockIdx.x;
+__device__ __forceinline__ long long pencil_base(const PassGeom& g, long long tile, int p) {
   if (g.inner == 1) {
     long long o = tile * g.W + p;
     return o < g.outer ? o * g.M : -1;
@@ -275,20 +276,29 @@ __device__ __forceinline__ long long pencil_base(const PassGeom& g, int p) {
 
 constexpr int kLoadBatch = 8;   // independent global accesses in flight per thread
 
+// Field loads.  NC: through the read-only data cache (the field is not
+// written while the kernel runs); otherwise L2-coherent loads (the batched
+// kernel reads fields that other CTAs of the same launch wrote).
+template <bool NC, typename S>
+__device__ __forceinline__ S ld_field(const S* p) {
+  if (NC) return __ldg(p);
+  return __ldcg(p);
+}
+
 // Global -> shared: element i of pencil p goes to chunk slot map(i) (space)
 // or map(i+1) (spectral).  Contiguous pencils (inner == 1): each pencil is
 // swept by the whole block; strided pencils: the W pencils of an element row
 // are adjacent in memory, so thread t serves pencil t mod W (W is a power of
 // two dividing the block size).  Loads are issued kLoadBatch at a time.
-template <typename T, int NORD>
-__device__ void load_tile(T* smr, const PassParams& P, bool spectral) {
+template <typename T, int NORD, bool NC>
+__device__ void load_tile(T* smr, const PassParams& P, long long tile, bool spectral) {
   constexpr int Q2 = 2 * (NORD / 2 + 1);
   const PassGeom& g = P.g;
   const int M = g.M;
   const int sh = spectral ? 1 : 0;
   if (g.inner == 1) {
     for (int p = 0; p < g.W; ++p) {
-      const long long base = pencil_base(g, p);
+      const long long base = pencil_base(g, tile, p);
       T* dst = smr + 2 * p * P.pitch;
       for (int i0 = threadIdx.x; i0 < M; i0 += kLoadBatch * blockDim.x) {
         T v[kLoadBatch];
@@ -297,8 +307,8 @@ __device__ void load_tile(T* smr, const PassParams& P, bool spectral) {
           const int i = i0 + u * blockDim.x;
           v[u] = T(0);
           if (i < M && base >= 0) {
-            if (P.in_f64) v[u] = T(__ldg(reinterpret_cast<const double*>(P.in) + base + i));
-            else v[u] = T(__ldg(reinterpret_cast<const float*>(P.in) + base + i));
+            if (P.in_f64) v[u] = T(ld_field<NC>(reinterpret_cast<const double*>(P.in) + base + i));
+            else v[u] = T(ld_field<NC>(reinterpret_cast<const float*>(P.in) + base + i));
           }
         }
 #pragma unroll
@@ -313,7 +323,7 @@ __device__ void load_tile(T* smr, const PassParams& P, bool spectral) {
   const int W = g.W;
   const int p = threadIdx.x & (W - 1);
   const int istep = blockDim.x / W;
-  const long long base = pencil_base(g, p);
+  const long long base = pencil_base(g, tile, p);
   const long long stride = g.inner;
   T* dst = smr + 2 * p * P.pitch;
   for (int i0 = threadIdx.x / W; i0 < M; i0 += kLoadBatch * istep) {
@@ -324,8 +334,8 @@ __device__ void load_tile(T* smr, const PassParams& P, bool spectral) {
       v[u] = T(0);
       if (i < M && base >= 0) {
         const long long off = base + (long long)i * stride;
-        if (P.in_f64) v[u] = T(__ldg(reinterpret_cast<const double*>(P.in) + off));
-        else v[u] = T(__ldg(reinterpret_cast<const float*>(P.in) + off));
+        if (P.in_f64) v[u] = T(ld_field<NC>(reinterpret_cast<const double*>(P.in) + off));
+        else v[u] = T(ld_field<NC>(reinterpret_cast<const float*>(P.in) + off));
       }
     }
 #pragma unroll
@@ -336,41 +346,42 @@ __device__ void load_tile(T* smr, const PassParams& P, bool spectral) {
   }
 }
 
-template <typename T>
+template <typename T, bool NC>
 __device__ __forceinline__ void store_one(const PassParams& P, long long off, T v) {
   if (P.out_f64) {
     double* o = reinterpret_cast<double*>(P.out) + off;
-    *o = P.accum ? *o + double(v) : double(v);
+    *o = P.accum ? (NC ? *o : __ldcg(o)) + double(v) : double(v);
   } else {
     float* o = reinterpret_cast<float*>(P.out) + off;
-    *o = P.accum ? *o + float(v) : float(v);
+    *o = P.accum ? (NC ? *o : __ldcg(o)) + float(v) : float(v);
   }
 }
 
-template <typename T, int NORD>
-__device__ void store_tile(const T* smr, const PassParams& P, bool spectral) {
+template <typename T, int NORD, bool NC>
+__device__ void store_tile(const T* smr, const PassParams& P, long long tile, bool spectral) {
   constexpr int Q2 = 2 * (NORD / 2 + 1);
   const PassGeom& g = P.g;
   const int M = g.M;
   const int sh = spectral ? 1 : 0;
   if (g.inner == 1) {
     for (int p = 0; p < g.W; ++p) {
-      const long long base = pencil_base(g, p);
+      const long long base = pencil_base(g, tile, p);
       if (base < 0) continue;
       const T* src = smr + 2 * p * P.pitch;
-      for (int i = threadIdx.x; i < M; i += blockDim.x) store_one<T>(P, base + i, src[chunk_slot<NORD, Q2>(i + sh)]);
+      for (int i = threadIdx.x; i < M; i += blockDim.x)
+        store_one<T, NC>(P, base + i, src[chunk_slot<NORD, Q2>(i + sh)]);
     }
     return;
   }
   const int W = g.W;
   const int p = threadIdx.x & (W - 1);
   const int istep = blockDim.x / W;
-  const long long base = pencil_base(g, p);
+  const long long base = pencil_base(g, tile, p);
   if (base < 0) return;
   const long long stride = g.inner;
   const T* src = smr + 2 * p * P.pitch;
   for (int i = threadIdx.x / W; i < M; i += istep)
-    store_one<T>(P, base + (long long)i * stride, src[chunk_slot<NORD, Q2>(i + sh)]);
+    store_one<T, NC>(P, base + (long long)i * stride, src[chunk_slot<NORD, Q2>(i + sh)]);
 }
 
 // Build the Q packed complex sequences of every pencil in place:
@@ -450,14 +461,13 @@ __device__ void reconstruct(cpx<T>* sm, const PassParams& P) {
 }
 
 template <typename T, int NORD>
-__device__ __forceinline__ T pencil_den_base(const PassParams& P, int p) {
+__device__ __forceinline__ T pencil_den_base(const PassParams& P, long long tile, int p) {
   // c + sum over the other axes of a_j mu_j[sigma_j] for the pencil p of this
   // CTA (fused pass on axis 0: the pencil index is the flat index of the
   // later axes), summed in float64.
   const PassGeom& g = P.g;
   long long w = 0;    // inner == 1: the later axes (if any) all have size 1
   if (g.inner > 1) {
-    long long tile = blockIdx.x;
     long long o = tile / g.tiles_inner;
     w = (tile - o * g.tiles_inner) * g.W + p;
     if (w >= g.inner) w = 0;
@@ -656,34 +666,41 @@ __device__ void pre_twiddle(cpx<T>* sm, const PassParams& P, const cpx<T>* rot) 
   __syncthreads();
 }
 
-template <typename T, int NORD, int MODE, int WM>
-__global__ void __launch_bounds__(pencil_threads<T>(), (pencil_min_blocks<T, MODE>())) pencil_pass_kernel(PassParams P) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T base[WM];
+// One tile of a pencil pass: W pencils loaded, transformed and stored.
+// smem_raw holds the pencils (W * pitch complex values) followed by the FFT
+// twiddles and DCT rotations (K complex values each), which are staged from
+// global memory unless stage_tables is false (the caller guarantees they are
+// still in place from the previous tile of the same pass).  base[] receives
+// the per-pencil denominator offsets of the fused pass.
+template <typename T, int NORD, int MODE, int WM, bool NC>
+__device__ __forceinline__ void pencil_tile(const PassParams& P, long long tile, unsigned char* smem_raw, T* base,
+                                            bool stage_tables) {
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smem_raw);
   T* smr = reinterpret_cast<T*>(smem_raw);
   constexpr int Q = NORD / 2 + 1;
   const int K = P.ax.K;
-  // FFT twiddles and DCT rotations, staged after the pencils
   cpx<T>* tw = sm + P.g.W * P.pitch;
   cpx<T>* rot = tw + K;
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    tw[i] = ld_cpx<T>(P.ax.tw, i);
-    rot[i] = ld_cpx<T>(P.ax.rot, i);
+  if (stage_tables) {
+    for (int i = threadIdx.x; i < K; i += blockDim.x) {
+      tw[i] = ld_cpx<T>(P.ax.tw, i);
+      rot[i] = ld_cpx<T>(P.ax.rot, i);
+    }
   }
-  if (MODE == MODE_FUSED && threadIdx.x < P.g.W) base[threadIdx.x] = pencil_den_base<T, NORD>(P, threadIdx.x);
+  constexpr bool DIVIDE = MODE == MODE_FUSED || MODE == MODE_FWD_DIV;
+  if (DIVIDE && threadIdx.x < P.g.W) base[threadIdx.x] = pencil_den_base<T, NORD>(P, tile, threadIdx.x);
   if (MODE == MODE_INV) {
-    load_tile<T, NORD>(smr, P, true);
+    load_tile<T, NORD, NC>(smr, P, tile, true);
     __syncthreads();
   } else {
-    load_tile<T, NORD>(smr, P, false);
+    load_tile<T, NORD, NC>(smr, P, tile, false);
     __syncthreads();
     build_sequences<T, NORD>(sm, P);
     fft_all<T>(sm, P, tw, P.g.W * Q, Q, true, false);
     post_twiddle<T, NORD>(sm, P, rot);
-    forward_map<T, NORD, MODE == MODE_FUSED, WM>(sm, P, base);
-    if (MODE == MODE_FWD) {
-      store_tile<T, NORD>(smr, P, true);
+    forward_map<T, NORD, DIVIDE, WM>(sm, P, base);
+    if (MODE == MODE_FWD || MODE == MODE_FWD_DIV) {
+      store_tile<T, NORD, NC>(smr, P, tile, true);
       return;
     }
   }
@@ -691,7 +708,14 @@ __global__ void __launch_bounds__(pencil_threads<T>(), (pencil_min_blocks<T, MOD
   pre_twiddle<T, NORD>(sm, P, rot);
   fft_all<T>(sm, P, tw, P.g.W * Q, Q, false, true);
   reconstruct<T, NORD>(sm, P);
-  store_tile<T, NORD>(smr, P, false);
+  store_tile<T, NORD, NC>(smr, P, tile, false);
+}
+
+template <typename T, int NORD, int MODE, int WM>
+__global__ void __launch_bounds__(pencil_threads<T>(), (pencil_min_blocks<T, MODE>())) pencil_pass_kernel(PassParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T base[WM];
+  pencil_tile<T, NORD, MODE, WM, true>(P, blockIdx.x, smem_raw, base, true);
 }
 
 }  // namespace femfft

@@ -1,0 +1,86 @@
+// The plan object and the host helpers shared by the plan API (api.cu) and
+// the batched scheduler (batch.cu).  Host code.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/femfft.h"
+#include "femfft_internal.h"
+#include "kernels.h"
+#include "pencil.cuh"
+
+namespace femfft {
+
+struct DevTables {
+  void* tw = nullptr;
+  void* rot = nullptr;
+  void* fwd = nullptr;
+  void* inv = nullptr;
+  void* mu = nullptr;
+};
+
+// One launch of a solve chain, recorded instead of launched: the batched
+// scheduler replays the recorded chains of many plans inside one persistent
+// kernel.  kind 0: pencil pass (pp, with the plan's own tile choice);
+// kind 1: operator apply (ap).
+struct RecordedOp {
+  int kind;
+  int mode, axis;
+  PassParams pp;
+  ApplyParams ap;
+};
+
+void set_last_error(const std::string& what);
+int cuda_fail(cudaError_t e, const char* what);
+
+// FFT schedule of length K with V values per thread: radix 3 passes first,
+// then radix 8 (if 8 | V), 4 (if 4 | V) and 2, greedily.  Returns false when
+// V does not divide K, exceeds kMaxV, or some radix needed does not divide V.
+bool fft_schedule_v(int K, int V, int* npass, int* radix);
+// The default schedule of the stand-alone passes (V = 8 for powers of two,
+// 12 or 6 with a factor 3).
+void fft_schedule(int K, int* V, int* npass, int* radix);
+
+// Tile geometry of a pass for W pencils per tile.
+void set_pass_tiles(PassParams& P, int W);
+
+// Records the mixed-precision solve of nrhs right-hand sides (b -> u, then
+// `steps` refinement steps) as the plan would launch it.  nrhs must not
+// exceed the plan's max_nrhs.  b and u may be placeholder addresses.
+int record_mixed_solve(fem_fft_plan p, const double* b, double* u, long long nrhs, int steps,
+                       std::vector<RecordedOp>* ops);
+
+}  // namespace femfft
+
+struct fem_fft_plan_s {
+  int N = 0, n = 0, precision = 0;
+  int64_t K[femfft::kMaxN] = {0, 0, 0}, M[femfft::kMaxN] = {0, 0, 0};
+  double X[femfft::kMaxN] = {1, 1, 1}, a[femfft::kMaxN] = {1, 1, 1}, c = 0.0;
+  int64_t max_nrhs = 1, dof = 0;
+  femfft::AxisHost ax[femfft::kMaxN];
+  femfft::DevTables t64[femfft::kMaxN], t32[femfft::kMaxN];
+  std::vector<double> Aref, Cref;      // element matrices
+  std::vector<double> Crow;            // exact row sums of Cref (those of Aref are 0)
+  float* w32 = nullptr;                // mixed workspace [max_nrhs][dof]
+  double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};   // float64 temporaries
+  double* d_scalars = nullptr;         // device scalars (norms, dots)
+  double rtol = 0.0;
+  int max_iter = 2;
+  int last_iters = -1;
+  double last_rel = -1.0;
+  int smem_optin = 0;
+  std::vector<void*> allocs;
+  // when set, pencil passes and applies are appended here instead of launched
+  std::vector<femfft::RecordedOp>* rec = nullptr;
+  // kernel timing (fem_fft_profile)
+  struct ProfRec {
+    cudaEvent_t a, b;
+    int kind;
+    double bytes, flops;
+  };
+  bool profiling = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> event_pool;
+};
