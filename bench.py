@@ -153,6 +153,43 @@ def oracle_full_solve(wl, b):
     return u, t_solve, t_basis
 
 
+def run_batched(torch, args, barrier):
+    """The batched workload (256 seeded problems, N in {2,3}, n in 2..8, K_i in
+    {16,...,512}, 1-8 right-hand sides): one graph launch of the batched
+    mixed solver against the same problems solved one after another with
+    stand-alone FP64 plans.  Right-hand sides N(0,1) drawn on the device."""
+    from paper_1701_03967_gb300 import Batch, Plan, synth
+    specs = synth.batched_problems()
+    plans = [Plan(s["n"], s["K"], s["X"], s["a"], s["c"], "mixed", max_nrhs=s["nrhs"]) for s in specs]
+    t0 = time.time()
+    batch = Batch(plans, [s["nrhs"] for s in specs])
+    t_create = time.time() - t0
+    g = torch.Generator(device="cuda").manual_seed(synth.SEED)
+    b = torch.randn(batch.total_len, dtype=torch.float64, device="cuda", generator=g)
+    u = torch.empty_like(b)
+    ms_b = time_steps(torch, lambda: batch.solve(b, out=u), max(2, args.steps // 2), args.warmup, barrier)
+    batch.check()
+    p64 = [Plan(s["n"], s["K"], s["X"], s["a"], s["c"], "fp64", max_nrhs=s["nrhs"]) for s in specs]
+    u64 = torch.empty_like(b)
+    views = list(zip(p64, batch.views(b), batch.views(u64)))
+
+    def seq64():
+        for pl, x, y in views:
+            pl.solve(x, out=y)
+    ms_64 = time_steps(torch, seq64, max(2, args.steps // 2), args.warmup, barrier)
+    rel = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
+    units = float(batch.total_len)
+    out = {"workload": "256 problems, N in {2,3}, n 2..8, K_i in {16,32,48,96,128,384,512}, 1-8 rhs",
+           "dof_x_rhs": batch.total_len, "steps": batch.n_steps, "items": batch.n_items,
+           "value": units / (ms_b * 1e-3), "unit": "DOF/s", "ms_per_solve": ms_b,
+           "fp64_sequential": {"value": units / (ms_64 * 1e-3), "ms_per_solve": ms_64},
+           "rel_vs_fp64": rel, "create_s": t_create, "launches_per_solve": len({s["n"] for s in specs})}
+    batch.close()
+    for pl in p64 + plans:
+        pl.close()
+    return out
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -220,6 +257,7 @@ def main():
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
     ap.add_argument("--refine", type=int, default=2, help="refinement steps of the mixed path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-problem batched measurement")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     args.warmup = max(args.warmup, 3)
@@ -271,6 +309,8 @@ def main():
     ms_e2e = time_steps(torch, e2e_step, args.steps, args.warmup, barrier)
     clk = clocks.stop()
 
+    batched = None if args.no_batched else run_batched(torch, args, barrier)
+
     if dist:
         t = torch.tensor([ms_mixed, ms_fp64, ms_e2e], device=f"cuda:{dev}")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -317,6 +357,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -127,6 +127,18 @@ int fem_fft_apply(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrh
 /* Refinement controls of the MIXED precision (ignored in FP64). */
 int fem_fft_set_refinement(fem_fft_plan plan, double rtol, int max_iter);
 
+/*
+ * fem_fft_set_residual_precision -- arithmetic of the refinement residual
+ * r = b - L u of a MIXED plan: FEM_FFT_RESIDUAL_DF64 (default) evaluates it in
+ * double-float arithmetic (pairs of floats, about 48 significant bits, on the
+ * float pipes: no float64 instruction), FEM_FFT_RESIDUAL_F64 in float64.  The
+ * refined solution's accuracy floor is ~1e-12 relative with DF64 and ~1e-13
+ * with F64 (2D, n = 9, K = 1024), both far below the 1e-10 target.
+ * fem_fft_apply is always float64.  Returns FEM_FFT_ERR_ARG for another mode.
+ */
+enum { FEM_FFT_RESIDUAL_F64 = 0, FEM_FFT_RESIDUAL_DF64 = 1 };
+int fem_fft_set_residual_precision(fem_fft_plan plan, int mode);
+
 /* Iterations and relative residual ||b - L u|| / ||b|| of the last MIXED
  * solve whose residual was evaluated (-1 if unknown).  Synchronises. */
 int fem_fft_last_info(fem_fft_plan plan, int* iters, double* rel_residual);

@@ -128,6 +128,12 @@ class Plan:
                    "fem_fft_plan_set_coefficients")
         self.a, self.c = a, float(c)
 
+    def set_residual_precision(self, mode="df64"):
+        """Arithmetic of the refinement residual of a mixed plan: "df64"
+        (double-float on the float pipes, default) or "f64"."""
+        code = {"f64": 0, "df64": 1}[mode]
+        _lib.check(_lib.lib().fem_fft_set_residual_precision(self._h, code), "fem_fft_set_residual_precision")
+
     def set_refinement(self, rtol=0.0, max_iter=2):
         _lib.check(_lib.lib().fem_fft_set_refinement(self._h, float(rtol), int(max_iter)),
                    "fem_fft_set_refinement")

@@ -408,6 +408,15 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
   const std::vector<double>& C = p->Cref;
   double s_[kMaxN];
   for (int i = 0; i < N; ++i) s_[i] = p->a[i] * 4.0 * p->K[i] * p->K[i] / (p->X[i] * p->X[i]);
+  // residual in double-float: every temporary is a double-float field, u and
+  // b are float64 fields split on load
+  const bool dfr = kind == 1 && p->residual_df;
+  auto dfify = [&](ApplyParams& P) {
+    if (!dfr) return;
+    P.df = 1;
+    P.plane = nrhs * p->dof;
+    for (int i = 0; i < kApplyMaxIn; ++i) P.in_df[i] = (P.in[i] && P.in[i] != u) ? 1 : 0;
+  };
   auto finish = [&](ApplyParams& P) {
     if (kind == 0) {
       P.out[0] = out;
@@ -431,12 +440,14 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
   if (N == 1) {
     ApplyParams P = one(0, u, nullptr, A, s_[0], &C, p->c);
     finish(P);
+    dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
     return FEM_FFT_OK;
   }
   double *X = p->tmp[0], *Y = p->tmp[1], *Z = p->tmp[2], *W = p->tmp[3];
   {
     ApplyParams P = one(0, u, X, A, s_[0], &C, p->c);                   // X = E_1 u
+    dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
   {
@@ -451,18 +462,21 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
     P.t_src[0] = 0; P.t_dst[0] = 0;
     set_mat(P, 1, A, s_[1], nullptr, 0.0, n1, p->Aref, p->Crow);
     P.t_src[1] = 1; P.t_dst[1] = 1;
+    dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
   if (N == 2) {
     ApplyParams P = one(0, Z, nullptr, C, 1.0, nullptr, 0.0);          // L u = Y + C_1 Z
     P.addend = Y;
     finish(P);
+    dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
     return FEM_FFT_OK;
   }
   {
     ApplyParams P = one(0, Z, Y, C, 1.0, nullptr, 0.0);                 // Y += C_1 Z
     P.addend = Y;
+    dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
   {
@@ -477,16 +491,19 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
     P.t_src[0] = 0; P.t_dst[0] = 0;
     set_mat(P, 1, A, s_[2], nullptr, 0.0, n1, p->Aref, p->Crow);
     P.t_src[1] = 1; P.t_dst[1] = 1;
+    dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
   {
     ApplyParams P = one(1, X, Z, C, 1.0, nullptr, 0.0);                 // Z = C_2 X
+    dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
   {
     ApplyParams P = one(0, Z, nullptr, C, 1.0, nullptr, 0.0);          // L u = W + C_1 Z
     P.addend = W;
     finish(P);
+    dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
   return FEM_FFT_OK;
@@ -736,6 +753,12 @@ int fem_fft_plan_set_coefficients(fem_fft_plan p, const double* h_a, double c, v
     p->a[i] = h_a[i];
   }
   p->c = c;
+  return FEM_FFT_OK;
+}
+
+int fem_fft_set_residual_precision(fem_fft_plan p, int mode) {
+  if (!p || (mode != FEM_FFT_RESIDUAL_F64 && mode != FEM_FFT_RESIDUAL_DF64)) return FEM_FFT_ERR_ARG;
+  p->residual_df = mode == FEM_FFT_RESIDUAL_DF64 ? 1 : 0;
   return FEM_FFT_OK;
 }
 

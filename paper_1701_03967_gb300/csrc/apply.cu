@@ -12,12 +12,55 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_kernel(ApplyParams P, 
   apply_block<NORD, NOUT, kApplyThreads, true>(P, TW, blockIdx.x, S);
 }
 
+template <int NORD, int NOUT>
+__global__ void __launch_bounds__(kApplyThreads, 2) apply_kernel_df(ApplyParams P, int TW) {
+  __shared__ ApplySmemDF<NORD, NOUT, kApplyThreads> S;
+  extern __shared__ uint2 tiles[];
+  apply_stage_mats_df<NORD, NOUT, kApplyThreads>(P, S);
+  apply_block_df<NORD, NOUT, kApplyThreads, true>(P, TW, blockIdx.x, S, tiles);
+}
+
+// dynamic shared memory of a double-float launch, enabling it once per kernel
+template <int NORD, int NOUT>
+int launch_apply_df(const ApplyParams& P, int TW, long long blocks, size_t smem, cudaStream_t s) {
+  static size_t enabled = 48 * 1024;
+  if (smem > enabled) {
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel_df<NORD, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    enabled = smem;
+  }
+  apply_kernel_df<NORD, NOUT><<<(unsigned)blocks, kApplyThreads, smem, s>>>(P, TW);
+  return 0;
+}
+
 int launch_apply(const ApplyParams& P, cudaStream_t s) {
   if (P.outer * (long long)P.K * P.inner <= 0) return 0;
   int TW = 1;
   while (TW * 2 <= 32 && TW * 2 <= P.inner) TW *= 2;
   const int TE = kApplyThreads / TW;
   const long long blocks = P.outer * ((P.inner + TW - 1) / TW) * ((P.K + TE - 1) / TE);
+  if (P.df) {
+    if (P.dotv || P.nout > 2) return (int)cudaErrorInvalidValue;
+    int nin = 0;
+    for (int i = 0; i < kApplyMaxIn; ++i) nin += P.in[i] != nullptr;
+    const size_t smem = apply_df_tile_bytes(P.n, TW, kApplyThreads, nin);
+    int rc = 0;
+    switch (P.n) {
+#define FEMFFT_APPLY_DF_CASE(NN)                                                       \
+  case NN:                                                                             \
+    rc = P.nout <= 1 ? launch_apply_df<NN, 1>(P, TW, blocks, smem, s)                  \
+                     : launch_apply_df<NN, 2>(P, TW, blocks, smem, s);                 \
+    if (rc) return rc;                                                                 \
+    break;
+      FEMFFT_APPLY_DF_CASE(1) FEMFFT_APPLY_DF_CASE(2) FEMFFT_APPLY_DF_CASE(3) FEMFFT_APPLY_DF_CASE(4)
+      FEMFFT_APPLY_DF_CASE(5) FEMFFT_APPLY_DF_CASE(6) FEMFFT_APPLY_DF_CASE(7) FEMFFT_APPLY_DF_CASE(8)
+      FEMFFT_APPLY_DF_CASE(9)
+#undef FEMFFT_APPLY_DF_CASE
+      default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+  }
   switch (P.n) {
 #define FEMFFT_APPLY_CASE(NN)                                                              \
   case NN:                                                                                 \

@@ -20,6 +20,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
 #include "kernels.h"
 
 namespace femfft {
@@ -263,6 +264,273 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
     block_accumulate<kApplyMaxOut>(dotacc, P.dots, &S.red[0][0]);
   } else if (P.norms) {
     double v2[2] = {rr, bb};
+    block_accumulate<2>(v2, P.norms, &S.red[0][0]);
+  }
+}
+
+// ---------------------------------------------------------- double-float
+// The same even/odd element products in double-float arithmetic (about 48
+// significant bits on the float pipes); used for the refinement residual.
+
+template <int NORD, int NOUT, int NTHREADS>
+struct ApplySmemDF {
+  using C = EO<NORD>;
+  df es[kApplyMaxTerms][C::R * C::SP];
+  df ea[kApplyMaxTerms][C::R * C::P];
+  df e1[kApplyMaxTerms][C::N1];
+  df row0[NOUT][NTHREADS];
+  double red[NTHREADS / 32][kApplyMaxOut];
+  int has1[kApplyMaxTerms];
+};
+
+__device__ __forceinline__ df split_entry(double m) {
+  const float hi = __double2float_rn(m);
+  return {hi, __double2float_rn(m - (double)hi)};
+}
+
+template <int NORD, int NOUT, int NTHREADS>
+__device__ __forceinline__ void apply_stage_mats_df(const ApplyParams& P, ApplySmemDF<NORD, NOUT, NTHREADS>& S) {
+  using C = EO<NORD>;
+  constexpr int N1 = C::N1;
+  for (int t = 0; t < P.nterm; ++t) {
+    for (int j = threadIdx.x; j < C::R * C::SP; j += blockDim.x) S.es[t][j] = split_entry(P.mats[t][j]);
+    for (int j = threadIdx.x; j < C::R * C::P; j += blockDim.x) S.ea[t][j] = split_entry(P.mats[t][C::R * C::SP + j]);
+    for (int r = threadIdx.x; r < N1; r += blockDim.x) S.e1[t][r] = split_entry(P.rows1[t][r]);
+    if (threadIdx.x == 0) {
+      int h = 0;
+      for (int r = 0; r < N1; ++r) h |= P.rows1[t][r] != 0.0;
+      S.has1[t] = h;
+    }
+  }
+}
+
+template <bool NC>
+__device__ __forceinline__ float ld_f32(const float* p) {
+  if (NC) return __ldg(p);
+  return __ldcg(p);
+}
+
+// one value of an input field: a double-float field (two planes) or a
+// float64 field split on load
+template <bool NC>
+__device__ __forceinline__ df ld_df(const double* x, bool is_df, long long plane, long long off) {
+  if (is_df) {
+    const float* f = reinterpret_cast<const float*>(x);
+    return {ld_f32<NC>(f + off), ld_f32<NC>(f + plane + off)};
+  }
+  return split_f64(ld_f64<NC>(x + off));
+}
+
+template <int NORD, bool NC>
+__device__ __forceinline__ void load_elem_df(const double* x, bool is_df, long long plane, long long line,
+                                             long long inner, int e, int M, df (&u)[NORD + 1]) {
+#pragma unroll
+  for (int q = 0; q <= NORD; ++q) {
+    const int g = NORD * e + q - 1;
+    u[q] = (g >= 0 && g < M) ? ld_df<NC>(x, is_df, plane, line + (long long)g * inner) : df{0.0f, 0.0f};
+  }
+}
+
+template <int NORD, bool ROW0_ONLY>
+__device__ __forceinline__ void elem_product_df(const df* Es, const df* Ea, const df* E1, bool has_e1,
+                                                const df (&u)[NORD + 1], df (&y)[NORD + 1]) {
+  using C = EO<NORD>;
+  const df ub = df_scale2(df_add(u[0], u[NORD]), 0.5f);
+  const df ub2 = df_scale2(ub, 2.0f);
+  df sv[C::P + 1], av[C::P];
+#pragma unroll
+  for (int j = 0; j < C::P; ++j) {
+    sv[j] = df_sub(df_add(u[j], u[NORD - j]), ub2);
+    av[j] = df_sub(u[j], u[NORD - j]);
+  }
+  sv[C::P] = (NORD % 2 == 0) ? df_sub(u[NORD / 2], ub) : df{0.0f, 0.0f};
+  constexpr int NS = (NORD % 2 == 0) ? C::SP : C::P;
+#pragma unroll
+  for (int q = 0; q < C::R; ++q) {
+    if (ROW0_ONLY && q > 0) break;
+    const df ts = df_dot<NS>(Es + q * C::SP, sv);
+    const df ta = df_dot<C::P>(Ea + q * C::P, av);
+    if (has_e1) {
+      y[q] = df_fma(ub, E1[q], df_add(ts, ta));
+      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = df_fma(ub, E1[NORD - q], df_sub(ts, ta));
+    } else {
+      y[q] = df_add(ts, ta);
+      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = df_sub(ts, ta);
+    }
+  }
+}
+
+// Input tiles of a double-float apply block, staged in shared memory before
+// any arithmetic so that all of the block's loads are in flight together
+// (the per-element loads of the unstaged form left the kernel waiting on
+// memory latency).  Rows: fine indices g0 = n e0 - 1 .. n (e0 + TE + 1) - 1,
+// i.e. the block's TE elements and the next element (whose row 0 the last
+// element row recomputes); columns: the block's TW positions of the
+// contiguous axis.  A slot holds 8 bytes: a float64 value or a (hi, lo)
+// float pair.
+__host__ __device__ constexpr int apply_df_rows(int n, int TE) { return n * (TE + 1) + 1; }
+inline size_t apply_df_tile_bytes(int n, int TW, int nthreads, int ninputs) {
+  return (size_t)ninputs * apply_df_rows(n, nthreads / TW) * TW * 8;
+}
+
+constexpr int kStageBatch = 8;   // loads in flight per thread while staging
+
+template <bool NC>
+__device__ void stage_input_df(const double* x, bool is_df, long long plane, long long line0, long long inner,
+                               int g0, int rows, int TW, int wvalid, int M, uint2* tile) {
+  const int total = rows * TW;
+  const int tw_shift = __ffs(TW) - 1;   // TW is a power of two
+  for (int i0 = threadIdx.x; i0 < total; i0 += kStageBatch * blockDim.x) {
+    uint2 v[kStageBatch];
+#pragma unroll
+    for (int k = 0; k < kStageBatch; ++k) {
+      const int i = i0 + k * blockDim.x;
+      const int r = i >> tw_shift, c = i & (TW - 1);
+      const int g = g0 + r;
+      v[k] = make_uint2(0u, 0u);
+      if (i < total && c < wvalid && g >= 0 && g < M) {
+        const long long off = line0 + (long long)g * inner + c;
+        if (is_df) {
+          const float* f = reinterpret_cast<const float*>(x);
+          v[k] = make_uint2(__float_as_uint(ld_f32<NC>(f + off)), __float_as_uint(ld_f32<NC>(f + plane + off)));
+        } else {
+          const unsigned long long bits = (unsigned long long)__double_as_longlong(ld_f64<NC>(x + off));
+          v[k] = make_uint2((unsigned)bits, (unsigned)(bits >> 32));
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kStageBatch; ++k) {
+      const int i = i0 + k * blockDim.x;
+      if (i < total) tile[i] = v[k];
+    }
+  }
+}
+
+__device__ __forceinline__ df slot_df(uint2 v, bool is_df) {
+  if (is_df) return {__uint_as_float(v.x), __uint_as_float(v.y)};
+  return split_f64(__longlong_as_double((long long)(((unsigned long long)v.y << 32) | v.x)));
+}
+
+template <int NORD>
+__device__ __forceinline__ void tile_elem_df(const uint2* tile, bool is_df, int TW, int te, int tw,
+                                             df (&u)[NORD + 1]) {
+#pragma unroll
+  for (int q = 0; q <= NORD; ++q) u[q] = slot_df(tile[(NORD * te + q) * TW + tw], is_df);
+}
+
+// Block bx of a double-float apply launch (same tiling as apply_block);
+// tiles: shared memory for the staged inputs (apply_df_tile_bytes).
+template <int NORD, int NOUT, int NTHREADS, bool NC>
+__device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, long long bx,
+                                               ApplySmemDF<NORD, NOUT, NTHREADS>& S, uint2* tiles) {
+  using C = EO<NORD>;
+  constexpr int N1 = C::N1;
+  const int K = P.K;
+  const int TE = NTHREADS / TW;
+  const long long wtiles = (P.inner + TW - 1) / TW;
+  const long long etiles = (K + TE - 1) / TE;
+  const long long et = bx % etiles;
+  bx /= etiles;
+  const long long wt = bx % wtiles;
+  const long long o = bx / wtiles;
+  const int tw = threadIdx.x % TW, te = threadIdx.x / TW;
+  const long long w0 = wt * TW;
+  const long long w = w0 + tw;
+  const int e = (int)(et * TE + te);
+  const bool valid = w < P.inner && e < K;
+  const long long line = o * (long long)P.M * P.inner + (valid ? w : 0);
+  const long long plane = P.plane;
+  const int rows = apply_df_rows(NORD, TE);
+  const int g0 = NORD * (int)(et * TE) - 1;
+  const int wvalid = (int)min((long long)TW, P.inner - w0);
+  // stage every input the block uses
+  uint2* tin[kApplyMaxIn];
+  {
+    int k = 0;
+    for (int i = 0; i < kApplyMaxIn; ++i) {
+      tin[i] = tiles + (size_t)k * rows * TW;
+      if (P.in[i]) {
+        stage_input_df<NC>(P.in[i], P.in_df[i] != 0, plane, o * (long long)P.M * P.inner + w0, P.inner, g0, rows,
+                           TW, wvalid, P.M, tin[i]);
+        ++k;
+      }
+    }
+  }
+  __syncthreads();
+
+  df acc[NOUT][N1];
+#pragma unroll
+  for (int j = 0; j < NOUT; ++j)
+#pragma unroll
+    for (int q = 0; q < N1; ++q) acc[j][q] = df{0.0f, 0.0f};
+  if (valid) {
+    for (int t = 0; t < P.nterm; ++t) {
+      df u[N1], y[N1];
+      const int src = P.t_src[t];
+      tile_elem_df<NORD>(tin[src], P.in_df[src] != 0, TW, te, tw, u);
+      elem_product_df<NORD, false>(S.es[t], S.ea[t], S.e1[t], S.has1[t], u, y);
+      const int d = P.t_dst[t];
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j)
+        if (j == d)
+#pragma unroll
+          for (int q = 0; q < N1; ++q) acc[j][q] = df_add(acc[j][q], y[q]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NOUT; ++j) S.row0[j][threadIdx.x] = acc[j][0];
+  __syncthreads();
+
+  float rr = 0.0f, bb = 0.0f;
+  if (valid) {
+    const bool has_node = e < K - 1;
+    if (has_node) {
+      if (te + 1 < TE) {
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) acc[j][NORD] = df_add(acc[j][NORD], S.row0[j][threadIdx.x + TW]);
+      } else {
+        for (int t = 0; t < P.nterm; ++t) {
+          df u[N1], y[N1];
+          const int src = P.t_src[t];
+          tile_elem_df<NORD>(tin[src], P.in_df[src] != 0, TW, te + 1, tw, u);
+          elem_product_df<NORD, true>(S.es[t], S.ea[t], S.e1[t], S.has1[t], u, y);
+          const int d = P.t_dst[t];
+#pragma unroll
+          for (int j = 0; j < NOUT; ++j)
+            if (j == d) acc[j][NORD] = df_add(acc[j][NORD], y[0]);
+        }
+      }
+    }
+    const int nrow = has_node ? NORD : NORD - 1;
+#pragma unroll
+    for (int r = 0; r < NORD; ++r) {
+      if (r >= nrow) break;
+      const long long off = line + (long long)(NORD * e + r) * P.inner;
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j) {
+        if (j < P.nout) {
+          df v = acc[j][r + 1];
+          if (j == 0 && P.addend) v = df_add(v, ld_df<NC>(P.addend, true, plane, off));
+          if (j == 0 && P.base) {
+            const df b = split_f64(ld_f64<NC>(&P.base[off]));
+            const float rv = df_to_float(df_sub(b, v));
+            rr = fmaf(rv, rv, rr);
+            bb = fmaf(b.hi, b.hi, bb);
+            P.out0_f32[off] = rv;
+          } else if (j == 0 && P.out0_f32) {
+            P.out0_f32[off] = df_to_float(v);
+          } else {
+            float* f = reinterpret_cast<float*>(P.out[j]);
+            f[off] = v.hi;
+            f[plane + off] = v.lo;
+          }
+        }
+      }
+    }
+  }
+  if (P.norms) {
+    double v2[2] = {(double)rr, (double)bb};
     block_accumulate<2>(v2, P.norms, &S.red[0][0]);
   }
 }

@@ -35,7 +35,7 @@ using namespace femfft;
 
 namespace {
 
-constexpr const char* kTuneVersion = "femfft-batch-tune-2";
+constexpr const char* kTuneVersion = "femfft-batch-tune-3";
 
 // Relocation tags: the chains are recorded with placeholder addresses
 // tag + byte offset for the right-hand sides (b) and solutions (u); every
@@ -72,11 +72,14 @@ size_t pencil_smem(const PassParams& P) {
   return (size_t)P.g.W * P.pitch * 2 * sizeof(float) + 2 * (size_t)P.ax.K * 2 * sizeof(float);
 }
 
-// Dynamic shared memory available to one CTA of the batch kernel of order n.
+// Dynamic shared memory available to one CTA of the batch kernel of order n
+// (kBatchCtasPerSm resident CTAs share an SM).
 size_t smem_budget(int n) {
-  int dev = 0, optin = 0;
+  int dev = 0, optin = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  optin = std::min(optin, per_sm / kBatchCtasPerSm - 1024);
   cudaFuncAttributes fa;
   std::memset(&fa, 0, sizeof(fa));
   const void* fn = kernel_for(n);
@@ -644,6 +647,11 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
         st.TW = TW;
         st.units = op.ap.outer * ((op.ap.inner + TW - 1) / TW) * ((op.ap.K + TE - 1) / TE);
         st.units_per_item = (int)std::max<long long>(1, kItemDof / ((long long)kBatchThreads * op.ap.n));
+        if (op.ap.df) {
+          int nin = 0;
+          for (int i = 0; i < kApplyMaxIn; ++i) nin += op.ap.in[i] != nullptr;
+          st.tile_smem = (int)apply_df_tile_bytes(op.ap.n, TW, kBatchThreads, nin);   // staged input tiles
+        }
         psteps[p].push_back(st);
       }
     }
@@ -671,6 +679,7 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
     for (size_t i = 0; i < total; ++i) {
       const BatchStage& st = psteps[probs[oprob[i]]][ostep[i]];
       if (st.kind == BATCH_PENCIL) g.smem = std::max(g.smem, pencil_smem(st.pp));
+      else g.smem = std::max(g.smem, batch_apply_smem<kMaxOrder>() + (size_t)st.tile_smem);
       g.stages.push_back(st);
       prev[i] = last[oprob[i]];
       last[oprob[i]] = (int)i;

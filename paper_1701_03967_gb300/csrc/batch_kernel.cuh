@@ -32,7 +32,8 @@
 
 namespace femfft {
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 256;
+constexpr int kBatchCtasPerSm = 2;   // two resident CTAs overlap one's prologue and barriers with the other's work
 constexpr long long kItemDof = 1 << 16;  // target unknowns per item
 constexpr unsigned kMaxSpin = 1u << 24;  // hard iteration bound of a dependency wait
 
@@ -46,7 +47,7 @@ struct BatchStage {
   int dep;            // index of the step this one waits for (-1: none)
   unsigned need;      // items of that step
   int units_per_item;
-  int pad;
+  int tile_smem;      // apply in double-float: bytes of its staged input tiles
   long long units;    // pass tiles or apply blocks
   long long first;    // first ticket
   long long items;
@@ -68,8 +69,14 @@ struct BatchArgs {
 // Dynamic shared memory of an apply item: matrices and exchange buffers,
 // then a copy of its parameters.
 template <int NORD>
+__host__ __device__ constexpr size_t batch_apply_scratch() {
+  return sizeof(ApplySmem<NORD, 2, kBatchThreads>) > sizeof(ApplySmemDF<NORD, 2, kBatchThreads>)
+             ? sizeof(ApplySmem<NORD, 2, kBatchThreads>)
+             : sizeof(ApplySmemDF<NORD, 2, kBatchThreads>);
+}
+template <int NORD>
 __host__ __device__ constexpr size_t batch_apply_smem() {
-  return sizeof(ApplySmem<NORD, 2, kBatchThreads>) + sizeof(ApplyParams);
+  return batch_apply_scratch<NORD>() + sizeof(ApplyParams);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -115,9 +122,20 @@ __device__ __forceinline__ void batch_apply_item(const ApplyParams& P, int TW, l
   }
 }
 
+template <int NORD, int NOUT>
+__device__ __forceinline__ void batch_apply_item_df(const ApplyParams& P, int TW, long long b0, long long b1,
+                                                    unsigned char* smem, uint2* tiles) {
+  auto& S = *reinterpret_cast<ApplySmemDF<NORD, NOUT, kBatchThreads>*>(smem);
+  apply_stage_mats_df<NORD, NOUT, kBatchThreads>(P, S);
+  for (long long b = b0; b < b1; ++b) {
+    apply_block_df<NORD, NOUT, kBatchThreads, false>(P, TW, b, S, tiles);
+    __syncthreads();
+  }
+}
+
 // The kernel for the problems of element order NORD: one item per CTA.
 template <int NORD>
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs A) {
+__global__ void __launch_bounds__(kBatchThreads, kBatchCtasPerSm) batch_kernel(BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_ticket;
   __shared__ int s_stage, s_abort;
@@ -156,13 +174,19 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs A) {
     else if (mode == MODE_FWD_DIV) pencil_tile<float, NORD, MODE_FWD_DIV, kMaxW, false>(s_pp, u0, smem, s_base, true);
     else pencil_tile<float, NORD, MODE_FUSED, kMaxW, false>(s_pp, u0, smem, s_base, true);
   } else {
-    ApplyParams* ap = reinterpret_cast<ApplyParams*>(smem + sizeof(ApplySmem<NORD, 2, kBatchThreads>));
+    ApplyParams* ap = reinterpret_cast<ApplyParams*>(smem + batch_apply_scratch<NORD>());
     const int* src = reinterpret_cast<const int*>(&S.ap);
     int* dst = reinterpret_cast<int*>(ap);
     for (int i = threadIdx.x; i < (int)(sizeof(ApplyParams) / sizeof(int)); i += blockDim.x) dst[i] = __ldg(&src[i]);
     __syncthreads();
-    if (mode <= 1) batch_apply_item<NORD, 1>(*ap, S.TW, u0, u1, smem);
-    else batch_apply_item<NORD, 2>(*ap, S.TW, u0, u1, smem);
+    if (ap->df) {
+      uint2* tiles = reinterpret_cast<uint2*>(smem + batch_apply_smem<NORD>());
+      if (mode <= 1) batch_apply_item_df<NORD, 1>(*ap, S.TW, u0, u1, smem, tiles);
+      else batch_apply_item_df<NORD, 2>(*ap, S.TW, u0, u1, smem, tiles);
+    } else {
+      if (mode <= 1) batch_apply_item<NORD, 1>(*ap, S.TW, u0, u1, smem);
+      else batch_apply_item<NORD, 2>(*ap, S.TW, u0, u1, smem);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {

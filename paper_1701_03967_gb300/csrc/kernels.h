@@ -42,6 +42,13 @@ struct ApplyParams {
   double* dots;
   long long outer, inner;
   int M, n, K;
+  // double-float arithmetic (df64.cuh): inputs with in_df[i] set, the
+  // outputs and the addend are double-float fields stored as two float
+  // planes (hi at the pointer, lo `plane` elements after it); other inputs
+  // and base are float64 and are split on load
+  int df;
+  int in_df[kApplyMaxIn];
+  long long plane;
 };
 
 int launch_apply(const ApplyParams& P, cudaStream_t s);

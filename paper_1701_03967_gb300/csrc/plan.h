@@ -68,6 +68,7 @@ struct fem_fft_plan_s {
   double* d_scalars = nullptr;         // device scalars (norms, dots)
   double rtol = 0.0;
   int max_iter = 2;
+  int residual_df = 1;                 // refinement residual in double-float (1) or float64 (0)
   int last_iters = -1;
   double last_rel = -1.0;
   int smem_optin = 0;

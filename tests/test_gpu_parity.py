@@ -177,3 +177,22 @@ def test_grad_coeffs_match_oracle(case):
     np.testing.assert_allclose(ga_g, ga, rtol=1e-10)
     np.testing.assert_allclose(gc_g, gc, rtol=1e-10)
     assert _rel(lam.cpu().numpy(), gf) <= 1e-12
+
+
+@pytest.mark.parametrize("case", [dict(n=9, K=(16, 32), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
+                                  dict(n=4, K=(8, 12, 8), a=(1.0, 2.0, 0.5), c=0.3),
+                                  dict(n=7, K=(48,), c=0.0)], ids=["2d_n9", "3d_n4", "1d_n7"])
+def test_mixed_residual_precisions(case):
+    """The refinement residual in float64 and in double-float arithmetic: both
+    reach the mixed-path target, and the two refined solutions agree to the
+    double-float floor."""
+    prob = _prob(case)
+    b = synth.normal_batch(2, prob.M, synth.CFG_TEST, 7)
+    want = osolve.solve(prob, b)
+    out = {}
+    for mode in ("f64", "df64"):
+        plan = _plan(case, "mixed", max_nrhs=2)
+        plan.set_residual_precision(mode)
+        out[mode] = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
+        assert _rel(out[mode], want) <= 1e-10, (mode, _rel(out[mode], want))
+    assert _rel(out["df64"], out["f64"]) <= 1e-11
