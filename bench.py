@@ -36,6 +36,7 @@ WORKLOADS = {
     "2d_mid": dict(name="2d_n9_K512x512_X1x2_a1x2.5_c1", n=9, K=(512, 512), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
 }
 FP64_PEAK_TFLOPS = 1.25     # nominal GB300 FP64 (profiling recipe table)
+FP32_LANE_TOPS = 152 * 128 * 2.07e9 / 1e12   # float32 lane operations per second at the maximum SM clock
 
 
 def _dist():
@@ -123,18 +124,31 @@ def roofline(prof, steps, peaks):
     if p["launches"] == 0 or p["ms"] <= 0:
         return None, kind
     per_launch_ms = p["ms"] / p["launches"]
+    share = p["ms"] / sum(v["ms"] for v in prof.values())
     if kind == "apply":
         achieved = p["flops64"] / p["launches"] / (per_launch_ms * 1e-3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (fp64)",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "apply_kernel (fp64 FMA)",
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table)",
-                "avg_launch_ms": per_launch_ms, "share_of_step": p["ms"] / sum(v["ms"] for v in prof.values())}, kind
+                "avg_launch_ms": per_launch_ms, "share_of_step": share}, kind
+    if kind == "apply_df":
+        # float32 lane operations of the double-float algorithm against the
+        # float32 issue rate: 152 SMs x 128 lanes x 2.07 GHz (recipe table)
+        achieved = p["flops64"] / p["launches"] / (per_launch_ms * 1e-3) / 1e12
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        gbs = p["bytes"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": FP32_LANE_TOPS, "unit": "Tops/s (fp32 lanes)",
+                "frac": achieved / FP32_LANE_TOPS, "traffic": None,
+                "kernel": "apply_kernel_df (double-float residual)",
+                "peak_source": "152 SMs x 128 fp32 lanes x 2.07 GHz (recipe table)",
+                "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm,
+                "avg_launch_ms": per_launch_ms, "share_of_step": share}, kind
     hbm = peaks.get("hbm_gbs", 6800.0)
     achieved = p["bytes"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             "traffic": None, "kernel": f"pencil_pass_kernel ({kind})",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
-            "avg_launch_ms": per_launch_ms, "share_of_step": p["ms"] / sum(v["ms"] for v in prof.values())}, kind
+            "avg_launch_ms": per_launch_ms, "share_of_step": share}, kind
 
 
 def oracle_full_solve(wl, b):
@@ -334,7 +348,8 @@ def main():
     launches = sum(v["launches"] for v in prof.values()) // max(args.steps, 1)
     kernels = {k: {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["ms"] / args.steps,
                    "GB_per_s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else None,
-                   "fp64_TFLOPs": (v["flops64"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] and v["flops64"] else None}
+                   ("fp32_Tops" if k == "apply_df" else "fp64_TFLOPs"):
+                       (v["flops64"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] and v["flops64"] else None}
                for k, v in prof.items()}
     if rank != 0:
         if dist:

@@ -188,12 +188,14 @@ int fem_fft_axis_precompute(int n, int64_t K, double X, double* h_lam, double* h
 /*
  * Kernel timing (tracing; no paper counterpart).  fem_fft_profile(plan, 1)
  * starts recording a CUDA event pair around every kernel the plan launches
- * (on the launch stream), with the algorithmic HBM bytes and float64 flops of
+ * (on the launch stream), with the algorithmic HBM bytes and arithmetic of
  * that launch; fem_fft_profile(plan, 0) stops and clears.  Kinds: 0 forward
  * pencil pass, 1 fused forward/divide/inverse pass, 2 inverse pass,
- * 3 matrix-free operator apply.  fem_fft_profile_read synchronises and
- * returns, for one kind, the launch count, summed device milliseconds,
- * summed algorithmic bytes and float64 flops (any pointer may be NULL).
+ * 3 matrix-free operator apply in float64 (arithmetic: float64 flops, FMA = 2),
+ * 4 operator apply in double-float (arithmetic: float32 operations of the
+ * double-float algorithm).  fem_fft_profile_read synchronises and returns,
+ * for one kind, the launch count, summed device milliseconds, summed
+ * algorithmic bytes and arithmetic (any pointer may be NULL).
  */
 int fem_fft_profile(fem_fft_plan plan, int enable);
 int fem_fft_profile_read(fem_fft_plan plan, int kind, int64_t* launches, double* ms, double* bytes,

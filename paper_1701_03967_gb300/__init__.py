@@ -154,7 +154,7 @@ class Plan:
                                                   ctypes.byref(gc), self._stream(stream)), "fem_fft_grad_coeffs")
         return list(ga), gc.value
 
-    KINDS = ("forward", "fused", "inverse", "apply")
+    KINDS = ("forward", "fused", "inverse", "apply", "apply_df")
 
     def profile(self, enable=True):
         """Start (or stop and clear) per-kernel CUDA-event timing."""

@@ -77,6 +77,18 @@ void fft_schedule(int K, int* V, int* npass, int* radix) {
   fft_schedule_v(K, v, npass, radix);
 }
 
+int tile_pitch(int K, int Q, int V, int W, bool strided, int elem_bytes) {
+  int pitch = pencil_pitch_min(K, Q);
+  const int B = elem_bytes == 4 ? 32 : 16;   // bank-wide slots of one wavefront
+  if (strided && K / V >= 32 && W >= 2 && W <= B / 2) {
+    const int mod = B / 2, want = (B / (2 * W)) % mod;
+    while (pitch % mod != want) ++pitch;
+    return pitch;
+  }
+  if (pitch % 2 == 0) pitch += 1;
+  return pitch;
+}
+
 void set_pass_tiles(PassParams& P, int W) {
   P.g.W = W;
   if (P.g.inner == 1) {
@@ -174,10 +186,8 @@ int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inn
   PassParams& P = pp->P;
   std::memset(&P, 0, sizeof(P));
   fft_schedule(K, &P.V, &P.npass, P.radix);
-  int pitch = pencil_pitch_min(K, Q);   // chunks plus bank padding
-  if (pitch % 2 == 0) pitch += 1;      // odd pitch spreads pencils over banks
-  P.pitch = pitch;
-  const size_t per_pen = (size_t)pitch * csize;
+  // per-pencil bound for the tile size; the pitch itself depends on W
+  const size_t per_pen = (size_t)(pencil_pitch_min(K, Q) + kPitchSlack) * csize;
   const size_t tables = 2 * (size_t)K * csize;   // twiddles and rotations staged in shared memory
   // shared memory per CTA: float passes keep two CTAs resident per SM
   const size_t per_sm = 226 * 1024;
@@ -223,6 +233,7 @@ int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inn
   P.g.inner = inner;
   P.g.M = M;
   set_pass_tiles(P, (int)W);
+  P.pitch = tile_pitch(K, Q, P.V, (int)W, inner > 1, f64 ? 8 : 4);
   const DevTables& d = f64 ? p->t64[axis] : p->t32[axis];
   P.ax.n = n;
   P.ax.K = K;
@@ -232,7 +243,7 @@ int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inn
   P.ax.fwd = d.fwd;
   P.ax.inv = d.inv;
   P.ax.mu = d.mu;
-  pp->smem = (size_t)W * per_pen + tables;
+  pp->smem = (size_t)W * P.pitch * csize + tables;
   pp->threads = threads;
   return FEM_FFT_OK;
 }
@@ -344,8 +355,25 @@ int apply_launch(fem_fft_plan p, const ApplyParams& P, cudaStream_t s) {
     const int ns = (n % 2 == 0) ? Pp + 1 : Pp;
     per_elem += 2.0 * R * ns + 2.0 * R * Pp + 3.0 * Pp + 2 + 2.0 * R + (mass ? 2.0 * R : 0.0);
   }
-  const double flops = elems / n * per_elem;
-  ProfScope scope(p, s, 3, bytes, flops);
+  double flops = elems / n * per_elem;
+  if (P.df) {
+    // float32 operations of the double-float algorithm (df64.cuh counts:
+    // df_add 11, df_fma 15, one Dot2 term 12, split of a float64 value 12)
+    // per element and term: load/split of the n+1 values, the centre value,
+    // the P sums and differences, the half-size products, the combination,
+    // the constant response of mass terms and the accumulation
+    double ops = 0.0;
+    for (int t = 0; t < P.nterm; ++t) {
+      bool mass = false;
+      for (int r = 0; r <= n; ++r) mass |= P.rows1[t][r] != 0.0;
+      const int ns = (n % 2 == 0) ? Pp + 1 : Pp;
+      const bool split = !P.in_df[P.t_src[t]];
+      ops += (split ? 12.0 * (n + 1) : 0.0) + 13.0 + 33.0 * Pp + (n % 2 == 0 ? 11.0 : 0.0) +
+             12.0 * R * (ns + Pp) + 22.0 * R + (mass ? 30.0 * R : 0.0) + 11.0 * (n + 1);
+    }
+    flops = elems / n * ops;
+  }
+  ProfScope scope(p, s, P.df ? 4 : 3, bytes, flops);
   return launch_apply(P, s);
 }
 
@@ -820,7 +848,7 @@ int fem_fft_profile(fem_fft_plan p, int enable) {
 }
 
 int fem_fft_profile_read(fem_fft_plan p, int kind, int64_t* launches, double* ms, double* bytes, double* flops) {
-  if (!p || kind < 0 || kind > 3) return FEM_FFT_ERR_ARG;
+  if (!p || kind < 0 || kind > 4) return FEM_FFT_ERR_ARG;
   int64_t cnt = 0;
   double t = 0, by = 0, fl = 0;
   for (auto& r : p->prof) {

@@ -35,7 +35,7 @@ using namespace femfft;
 
 namespace {
 
-constexpr const char* kTuneVersion = "femfft-batch-tune-3";
+constexpr const char* kTuneVersion = "femfft-batch-tune-4";
 
 // Relocation tags: the chains are recorded with placeholder addresses
 // tag + byte offset for the right-hand sides (b) and solutions (u); every
@@ -110,7 +110,9 @@ int max_tile_w(const PassParams& P, size_t budget) {
   const int K = P.ax.K;
   long long w = kMaxW;
   w = std::min<long long>(w, (long long)kMaxChunkTasks * kBatchThreads / K);
-  const size_t per_pen = (size_t)P.pitch * 2 * sizeof(float), tables = 2 * (size_t)K * 2 * sizeof(float);
+  const int Q = P.ax.n / 2 + 1;
+  const size_t per_pen = (size_t)(pencil_pitch_min(K, Q) + kPitchSlack) * 2 * sizeof(float);
+  const size_t tables = 2 * (size_t)K * 2 * sizeof(float);
   if (budget <= tables) return 0;
   w = std::min<long long>(w, (long long)((budget - tables) / per_pen));
   if (P.g.inner > 1) {
@@ -132,6 +134,7 @@ bool set_tile(PassParams& P, int W, int V, size_t budget) {
   P.npass = npass;
   for (int i = 0; i < kMaxRadixPasses; ++i) P.radix[i] = i < npass ? radix[i] : 0;
   set_pass_tiles(P, W);
+  P.pitch = tile_pitch(K, P.ax.n / 2 + 1, V, W, P.g.inner > 1, 4);
   return true;
 }
 

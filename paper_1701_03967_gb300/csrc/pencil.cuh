@@ -411,8 +411,17 @@ __device__ void build_sequences(cpx<T>* sm, const PassParams& P) {
       int p = c / K, e = c - p * K;
       T* smr = reinterpret_cast<T*>(sm + p * P.pitch) + 2 * cofs(e, Q);
       T y[NORD];
+      {
+        // the chunk starts on a complex boundary: read it in (re, im) pairs
+        const cpx<T>* cv = reinterpret_cast<const cpx<T>*>(smr);
 #pragma unroll
-      for (int s = 0; s < NORD; ++s) y[s] = smr[s];
+        for (int s = 0; s + 1 < NORD; s += 2) {
+          const cpx<T> c2 = cv[s / 2];
+          y[s] = c2.re;
+          y[s + 1] = c2.im;
+        }
+        if (NORD % 2) y[NORD - 1] = smr[NORD - 1];
+      }
       T xr = (e < K - 1) ? y[NORD - 1] : T(0);
       T sg = (e & 1) ? T(-1) : T(1);
       cpx<T> out[Q];
@@ -444,18 +453,22 @@ __device__ void reconstruct(cpx<T>* sm, const PassParams& P) {
 #pragma unroll
     for (int q = 0; q < Q; ++q) x[q] = ch[q];
     T sg = (e & 1) ? T(-1) : T(1);
-    T* smr = reinterpret_cast<T*>(ch);
-    smr[NORD - 1] = sg * x[0].re + x[0].im;
+    T y[NORD];
+    y[NORD - 1] = sg * x[0].re + x[0].im;
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
       T ys = sg * x[q].re, yc = x[q].im;
       if (2 * q < NORD) {
-        smr[q - 1] = ys + yc;
-        smr[NORD - q - 1] = ys - yc;
+        y[q - 1] = ys + yc;
+        y[NORD - q - 1] = ys - yc;
       } else {
-        smr[q - 1] = ys;
+        y[q - 1] = ys;
       }
     }
+    // written back in (re, im) pairs
+#pragma unroll
+    for (int s = 0; s + 1 < NORD; s += 2) ch[s / 2] = cpx<T>{y[s], y[s + 1]};
+    if (NORD % 2) reinterpret_cast<T*>(ch)[NORD - 1] = y[NORD - 1];
   }
   __syncthreads();
 }

@@ -46,6 +46,15 @@ void fft_schedule(int K, int* V, int* npass, int* radix);
 // Tile geometry of a pass for W pencils per tile.
 void set_pass_tiles(PassParams& P, int W);
 
+// Complex values per pencil in shared memory for a tile of W pencils.  The
+// strided tile loads and stores put W pencils times 32 / W rows in a warp;
+// a pitch with 2 pitch = 32 / W (mod 32) banks (float; 16 / W in 8-byte
+// units for double) puts them in disjoint bank ranges.  Where a warp spans
+// several FFT sequences (K / V < 32) or W is 1, the pitch is odd instead.
+// At most kPitchSlack above K * Q.
+constexpr int kPitchSlack = 16;
+int tile_pitch(int K, int Q, int V, int W, bool strided, int elem_bytes);
+
 // Records the mixed-precision solve of nrhs right-hand sides (b -> u, then
 // `steps` refinement steps) as the plan would launch it.  nrhs must not
 // exceed the plan's max_nrhs.  b and u may be placeholder addresses.
