@@ -99,6 +99,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(torch, dist, values, device):
+    """Every rank's timings -> the per-quantity maximum over ranks (the job's
+    time is its slowest replica's)."""
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_value(units_per_rank, world_size, ms):
+    """Whole-job throughput: the units every replica processed / the slowest
+    replica's time."""
+    return world_size * units_per_rank / (ms * 1e-3)
+
+
 def time_steps(torch, fn, steps, warmup, barrier=None):
     for _ in range(warmup):
         fn()
@@ -117,7 +131,13 @@ def time_steps(torch, fn, steps, warmup, barrier=None):
     return ev0.elapsed_time(ev1) / steps
 
 
-def roofline(prof, steps, peaks):
+# DRAM bytes (read + write) per DOF of one double-float residual apply, the
+# average of the three launches of a 2D n=9 residual chain, from ncu
+# (profiles/apply_kernel_df_2d_n9_K512.md: 510.7 MB per launch at 21.2 M DOF)
+APPLY_DF_TRAFFIC_PER_DOF_2D_N9 = 510.7e6 / 21224449
+
+
+def roofline(prof, steps, peaks, wl=None):
     """Dominant kernel kind of the step and its achieved fraction of its bound."""
     kind = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[kind]
@@ -132,13 +152,17 @@ def roofline(prof, steps, peaks):
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table)",
                 "avg_launch_ms": per_launch_ms, "share_of_step": share}, kind
     if kind == "apply_df":
+        traffic = None
+        if wl is not None and wl["n"] == 9 and len(wl["K"]) == 2:
+            dof = (wl["n"] * wl["K"][0] - 1) * (wl["n"] * wl["K"][1] - 1)
+            traffic = APPLY_DF_TRAFFIC_PER_DOF_2D_N9 * dof
         # float32 lane operations of the double-float algorithm against the
         # float32 issue rate: 152 SMs x 128 lanes x 2.07 GHz (recipe table)
         achieved = p["flops64"] / p["launches"] / (per_launch_ms * 1e-3) / 1e12
         hbm = peaks.get("hbm_gbs", 6800.0)
         gbs = p["bytes"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
         return {"bound": "alu", "achieved": achieved, "peak": FP32_LANE_TOPS, "unit": "Tops/s (fp32 lanes)",
-                "frac": achieved / FP32_LANE_TOPS, "traffic": None,
+                "frac": achieved / FP32_LANE_TOPS, "traffic": traffic,
                 "kernel": "apply_kernel_df (double-float residual)",
                 "peak_source": "152 SMs x 128 fp32 lanes x 2.07 GHz (recipe table)",
                 "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm,
@@ -326,9 +350,7 @@ def main():
     batched = None if args.no_batched else run_batched(torch, args, barrier)
 
     if dist:
-        t = torch.tensor([ms_mixed, ms_fp64, ms_e2e], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_mixed, ms_fp64, ms_e2e = (float(x) for x in t.tolist())
+        ms_mixed, ms_fp64, ms_e2e = max_over_ranks(torch, dist, [ms_mixed, ms_fp64, ms_e2e], f"cuda:{dev}")
 
     u_mixed = u.cpu().numpy()
     u_fp64 = u64.cpu().numpy()
@@ -344,7 +366,7 @@ def main():
                          f"{t_solve:.1f} s; eigenbasis {t_basis:.1f} s untimed)"}
 
     peaks = _peaks()
-    roof, dom = roofline(prof, args.steps, peaks)
+    roof, dom = roofline(prof, args.steps, peaks, wl)
     launches = sum(v["launches"] for v in prof.values()) // max(args.steps, 1)
     kernels = {k: {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["ms"] / args.steps,
                    "GB_per_s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else None,
@@ -356,16 +378,16 @@ def main():
             dist.destroy_process_group()
         return
     line = {
-        "metric": METRIC, "value": ws * dof / (ms_mixed * 1e-3), "unit": "DOF/s", "n_gpus": ws,
+        "metric": METRIC, "value": job_value(dof, ws, ms_mixed), "unit": "DOF/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": wl["name"], "n": wl["n"], "K": list(wl["K"]), "X": list(wl["X"]),
                    "a": list(wl["a"]), "c": wl["c"], "dof": dof, "nrhs": 1, "precision": "mixed",
                    "refine_steps": args.refine, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (b and u 680 MB each, float32 workspace 340 MB)"},
-        "fp64": {"value": ws * dof / (ms_fp64 * 1e-3), "unit": "DOF/s", "ms_per_step": ms_fp64, "dtype": "f64"},
+        "fp64": {"value": job_value(dof, ws, ms_fp64), "unit": "DOF/s", "ms_per_step": ms_fp64, "dtype": "f64"},
         "accuracy": acc,
-        "e2e": {"value": ws * dof / (ms_e2e * 1e-3), "unit": "DOF/s", "h2d_bytes_per_step": dof * 8,
+        "e2e": {"value": job_value(dof, ws, ms_e2e), "unit": "DOF/s", "h2d_bytes_per_step": dof * 8,
                 "d2h_bytes_per_step": dof * 8},
         "roofline": roof,
         "kernels": kernels,
