@@ -235,6 +235,69 @@ def cores():
         return os.cpu_count()
 
 
+def run_other_workloads(torch, args, barrier):
+    """The other configurations, timed like the headline (device-resident
+    N(0,1) right-hand sides, CUDA events): the n = 1..9 sweep of the 2D
+    workload at K = 1024 x 1024, the 3D workloads n=9 K=64^3 and n=4 K=128^3
+    (mixed and FP64), and one differentiation step (forward solve + adjoint
+    solve + coefficient gradients) of 3D n=5 K=64^3 in mixed precision."""
+    from paper_1701_03967_gb300 import Plan, fem_solve
+    g = torch.Generator(device="cuda").manual_seed(1701)
+    steps = max(2, args.steps // 2)
+
+    def pair(n, K, X, a, c):
+        out = {}
+        ref = None
+        for prec in ("mixed", "fp64"):
+            pl = Plan(n, K, X, a, c, precision=prec)
+            b = torch.randn(pl.M, dtype=torch.float64, device="cuda", generator=g) if ref is None else ref[0]
+            u = torch.empty_like(b)
+            ms = time_steps(torch, lambda: pl.solve(b, out=u), steps, args.warmup, barrier)
+            out[prec] = {"ms": ms, "dof_per_s": pl.dof / (ms * 1e-3)}
+            if ref is None:
+                ref = (b, u.clone())
+            else:
+                out["mixed_vs_fp64_rel"] = float(torch.linalg.vector_norm(ref[1] - u) / torch.linalg.vector_norm(u))
+            pl.close()
+        out["dof"] = (n * K[0] - 1) * (n * K[1] - 1) * ((n * K[2] - 1) if len(K) == 3 else 1)
+        return out
+
+    res = {"sweep_2d_K1024": {}}
+    for n in range(1, 10):
+        res["sweep_2d_K1024"][f"n{n}"] = pair(n, (1024, 1024), (1.0, 2.0), (1.0, 2.5), 1.0)
+        torch.cuda.empty_cache()
+    res["3d_n9_K64"] = pair(9, (64, 64, 64), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.0)
+    torch.cuda.empty_cache()
+    res["3d_n4_K128"] = pair(4, (128, 128, 128), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.0)
+    torch.cuda.empty_cache()
+    pl = Plan(5, (64, 64, 64), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.0, precision="mixed")
+    f = torch.randn(pl.M, dtype=torch.float64, device="cuda", generator=g).requires_grad_(True)
+    ut = torch.randn(pl.M, dtype=torch.float64, device="cuda", generator=g)
+    av = torch.ones(3, dtype=torch.float64, requires_grad=True)
+    cv = torch.zeros((), dtype=torch.float64, requires_grad=True)
+
+    def grad_step():
+        loss = torch.sum((fem_solve(pl, f, av, cv) - ut) ** 2)
+        loss.backward()
+    ms = time_steps(torch, grad_step, steps, args.warmup, barrier)
+    res["grad_3d_n5_K64"] = {"ms": ms, "dof": pl.dof, "note": "loss.backward() of ||u - u_t||^2, u = L(a, c)^-1 f"}
+    pl.close()
+    return res
+
+
+def workload_config(wl, args, ws):
+    """The `config` object of both arms' JSON lines."""
+    dof = 1
+    for k in wl["K"]:
+        dof *= wl["n"] * k - 1
+    mb = dof * 8 / 1e6
+    return {"workload": wl["name"], "n": wl["n"], "K": list(wl["K"]), "X": list(wl["X"]),
+            "a": list(wl["a"]), "c": wl["c"], "dof": dof, "nrhs": 1, "precision": "mixed",
+            "refine_steps": args.refine, "parallelism": f"replicas x{ws}",
+            "l2": f"inputs larger than L2 (b and u {mb:.0f} MB each, float32 workspace {mb / 2:.0f} MB)"
+                  if mb > 129 else f"inputs of {mb:.1f} MB, within L2"}
+
+
 def run_reference(args, wl):
     """Reference arm: the FP64 CPU oracle timed on the host cores.  Each step
     is one of the four dense axis products of the oracle's solve (a quarter of
@@ -278,7 +341,7 @@ def run_reference(args, wl):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "dof": dof, "nrhs": 1},
+            "config": workload_config(wl, args, ws),
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores(), "kind": "oracle",
                              "sample": f"one of the {nst} dense axis products of the oracle solve per step "
                                        f"(credited DOF/{nst}); eigenbasis precomputed untimed"},
@@ -296,6 +359,7 @@ def main():
     ap.add_argument("--refine", type=int, default=2, help="refinement steps of the mixed path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-problem batched measurement")
+    ap.add_argument("--no-others", action="store_true", help="skip the n-sweep, 3D and gradient measurements")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     args.warmup = max(args.warmup, 3)
@@ -348,6 +412,7 @@ def main():
     clk = clocks.stop()
 
     batched = None if args.no_batched else run_batched(torch, args, barrier)
+    others = None if args.no_others else run_other_workloads(torch, args, barrier)
 
     if dist:
         ms_mixed, ms_fp64, ms_e2e = max_over_ranks(torch, dist, [ms_mixed, ms_fp64, ms_e2e], f"cuda:{dev}")
@@ -381,10 +446,7 @@ def main():
         "metric": METRIC, "value": job_value(dof, ws, ms_mixed), "unit": "DOF/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": wl["name"], "n": wl["n"], "K": list(wl["K"]), "X": list(wl["X"]),
-                   "a": list(wl["a"]), "c": wl["c"], "dof": dof, "nrhs": 1, "precision": "mixed",
-                   "refine_steps": args.refine, "parallelism": f"replicas x{ws}",
-                   "l2": "inputs larger than L2 (b and u 680 MB each, float32 workspace 340 MB)"},
+        "config": workload_config(wl, args, ws),
         "fp64": {"value": job_value(dof, ws, ms_fp64), "unit": "DOF/s", "ms_per_step": ms_fp64, "dtype": "f64"},
         "accuracy": acc,
         "e2e": {"value": job_value(dof, ws, ms_e2e), "unit": "DOF/s", "h2d_bytes_per_step": dof * 8,
@@ -395,6 +457,7 @@ def main():
         "clocks": clk,
         "cpu_baseline": cpu,
         "batched": batched,
+        "other_workloads": others,
     }
     print(json.dumps(line), flush=True)
     if dist:

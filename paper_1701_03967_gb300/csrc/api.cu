@@ -89,6 +89,22 @@ int tile_pitch(int K, int Q, int V, int W, bool strided, int elem_bytes) {
   return pitch;
 }
 
+void set_fft_passes(PassParams& P) {
+  int prod = 1;
+  for (int ps = 0; ps < kMaxRadixPasses; ++ps) {
+    if (ps < P.npass) {
+      P.pprod[ps] = prod;
+      P.pmask[ps] = (prod & (prod - 1)) == 0 ? prod - 1 : -1;
+      P.pstride[ps] = P.ax.K / (prod * P.radix[ps]);
+      prod *= P.radix[ps];
+    } else {
+      P.pprod[ps] = 0;
+      P.pmask[ps] = 0;
+      P.pstride[ps] = 0;
+    }
+  }
+}
+
 void set_pass_tiles(PassParams& P, int W) {
   P.g.W = W;
   if (P.g.inner == 1) {
@@ -238,6 +254,7 @@ int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inn
   P.ax.n = n;
   P.ax.K = K;
   P.ax.M = M;
+  set_fft_passes(P);
   P.ax.tw = d.tw;
   P.ax.rot = d.rot;
   P.ax.fwd = d.fwd;

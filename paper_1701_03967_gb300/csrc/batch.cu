@@ -35,7 +35,7 @@ using namespace femfft;
 
 namespace {
 
-constexpr const char* kTuneVersion = "femfft-batch-tune-4";
+constexpr const char* kTuneVersion = "femfft-batch-tune-5";
 
 // Relocation tags: the chains are recorded with placeholder addresses
 // tag + byte offset for the right-hand sides (b) and solutions (u); every
@@ -133,6 +133,7 @@ bool set_tile(PassParams& P, int W, int V, size_t budget) {
   P.V = V;
   P.npass = npass;
   for (int i = 0; i < kMaxRadixPasses; ++i) P.radix[i] = i < npass ? radix[i] : 0;
+  set_fft_passes(P);
   set_pass_tiles(P, W);
   P.pitch = tile_pitch(K, P.ax.n / 2 + 1, V, W, P.g.inner > 1, 4);
   return true;

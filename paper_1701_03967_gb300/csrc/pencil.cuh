@@ -103,6 +103,11 @@ struct PassParams {
   int V;             // FFT values per thread
   int npass;
   int radix[kMaxRadixPasses];
+  // per pass: product of the earlier radices, its mask when a power of two
+  // (else -1), and the twiddle stride K / (prod * radix) (set_fft_passes)
+  int pprod[kMaxRadixPasses];
+  int pmask[kMaxRadixPasses];
+  int pstride[kMaxRadixPasses];
   int in_f64, out_f64, accum;
 };
 
@@ -155,6 +160,8 @@ __device__ __forceinline__ void dft8(cpx<T>* u) {
 
 // Complex offset of chunk k within a pencil (chunks are Q complex values
 // long; Q is odd for odd n, which keeps the unit-stride passes conflict-free).
+// Padding every 16 chunks removed most bank conflicts of the first radix
+// pass but cost more in index arithmetic than it saved (measured).
 __host__ __device__ __forceinline__ int cofs(int k, int Q) { return k * Q; }
 __host__ __device__ __forceinline__ int pencil_pitch_min(int K, int Q) { return cofs(K, Q); }
 
@@ -170,9 +177,10 @@ __device__ __forceinline__ int makhoul_perm(int r, int K) {
 // twiddles them by exp(-2 pi i r (i mod prod) / (prod R)), applies the
 // R-point DFT and writes element (i - i mod prod) R + (i mod prod) + r prod.
 // Sequence elements are Q complex values apart.
-template <typename T, int R>
-__device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassParams& P, const cpx<T>* tw, int Q,
-                                         int tau, int tps, int prod, bool perm_in, bool perm_out) {
+template <typename T, int R, int Q>
+__device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassParams& P, const cpx<T>* tw,
+                                         int tau, int tps, int prod, int mask, int stride, bool perm_in,
+                                         bool perm_out) {
   const int K = P.ax.K;
   const int T_ = K / R;
   const int nb = P.V / R;
@@ -194,12 +202,11 @@ __device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassPa
   }
   __syncthreads();
   if (active) {
-    const int stride = K / (prod * R);
 #pragma unroll
     for (int g = 0; g < GMAX; ++g) {
       if (g < nb) {
         const int i = tau + g * tps;
-        const int kk = i % prod;
+        const int kk = mask >= 0 ? (i & mask) : i % prod;
         if (prod > 1) {
 #pragma unroll
           for (int r = 1; r < R; ++r) u[g * R + r] = cmul(u[g * R + r], tw[r * kk * stride]);
@@ -226,9 +233,8 @@ __device__ __forceinline__ void fft_pass(cpx<T>* base, bool active, const PassPa
 // perm_in: the first pass reads element makhoul_perm(idx) (DCT-II input
 // reordering); perm_out: the last pass writes element makhoul_perm(idx)
 // (DCT-III output reordering).
-template <typename T>
-__device__ void fft_all(cpx<T>* sm, const PassParams& P, const cpx<T>* tw, int nseq, int Q, bool perm_in,
-                        bool perm_out) {
+template <typename T, int Q>
+__device__ void fft_all(cpx<T>* sm, const PassParams& P, const cpx<T>* tw, int nseq, bool perm_in, bool perm_out) {
   const int K = P.ax.K;
   const int tps = K / P.V;                  // tasks per sequence
   const int spr = blockDim.x / tps;         // sequences per round (host: >= 1)
@@ -242,15 +248,14 @@ __device__ void fft_all(cpx<T>* sm, const PassParams& P, const cpx<T>* tw, int n
       int pen = seq / Q, q = seq - pen * Q;
       base = sm + pen * P.pitch + q;
     }
-    int prod = 1;
     for (int ps = 0; ps < P.npass; ++ps) {
       const int R = P.radix[ps];
+      const int prod = P.pprod[ps], mask = P.pmask[ps], stride = P.pstride[ps];
       const bool pin = perm_in && ps == 0, pout = perm_out && ps == P.npass - 1;
-      if (R == 8) fft_pass<T, 8>(base, active, P, tw, Q, tau, tps, prod, pin, pout);
-      else if (R == 4) fft_pass<T, 4>(base, active, P, tw, Q, tau, tps, prod, pin, pout);
-      else if (R == 3) fft_pass<T, 3>(base, active, P, tw, Q, tau, tps, prod, pin, pout);
-      else fft_pass<T, 2>(base, active, P, tw, Q, tau, tps, prod, pin, pout);
-      prod *= R;
+      if (R == 8) fft_pass<T, 8, Q>(base, active, P, tw, tau, tps, prod, mask, stride, pin, pout);
+      else if (R == 4) fft_pass<T, 4, Q>(base, active, P, tw, tau, tps, prod, mask, stride, pin, pout);
+      else if (R == 3) fft_pass<T, 3, Q>(base, active, P, tw, tau, tps, prod, mask, stride, pin, pout);
+      else fft_pass<T, 2, Q>(base, active, P, tw, tau, tps, prod, mask, stride, pin, pout);
     }
   }
 }
@@ -709,7 +714,7 @@ __device__ __forceinline__ void pencil_tile(const PassParams& P, long long tile,
     load_tile<T, NORD, NC>(smr, P, tile, false);
     __syncthreads();
     build_sequences<T, NORD>(sm, P);
-    fft_all<T>(sm, P, tw, P.g.W * Q, Q, true, false);
+    fft_all<T, Q>(sm, P, tw, P.g.W * Q, true, false);
     post_twiddle<T, NORD>(sm, P, rot);
     forward_map<T, NORD, DIVIDE, WM>(sm, P, base);
     if (MODE == MODE_FWD || MODE == MODE_FWD_DIV) {
@@ -719,7 +724,7 @@ __device__ __forceinline__ void pencil_tile(const PassParams& P, long long tile,
   }
   inverse_map<T, NORD, WM>(sm, P);
   pre_twiddle<T, NORD>(sm, P, rot);
-  fft_all<T>(sm, P, tw, P.g.W * Q, Q, false, true);
+  fft_all<T, Q>(sm, P, tw, P.g.W * Q, false, true);
   reconstruct<T, NORD>(sm, P);
   store_tile<T, NORD, NC>(smr, P, tile, false);
 }

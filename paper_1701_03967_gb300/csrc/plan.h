@@ -46,6 +46,11 @@ void fft_schedule(int K, int* V, int* npass, int* radix);
 // Tile geometry of a pass for W pencils per tile.
 void set_pass_tiles(PassParams& P, int W);
 
+// Per-pass FFT index data of P's radix schedule (P.ax.K, P.npass, P.radix):
+// prod = product of the earlier radices, its mask when a power of two (else
+// -1), twiddle stride K / (prod * radix).
+void set_fft_passes(PassParams& P);
+
 // Complex values per pencil in shared memory for a tile of W pencils.  The
 // strided tile loads and stores put W pencils times 32 / W rows in a warp;
 // a pitch with 2 pitch = 32 / W (mod 32) banks (float; 16 / W in 8-byte
