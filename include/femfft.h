@@ -124,6 +124,17 @@ int fem_fft_solve(fem_fft_plan plan, const double* d_b, double* d_u, int64_t nrh
  * form; element blocks of Section 2).  d_u != d_b. */
 int fem_fft_apply(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrhs, void* stream);
 
+/*
+ * fem_fft_apply_mass -- d_b = (calC_1 (x) ... (x) calC_N) d_u in float64,
+ * matrix-free: the mass operator of the N-D space (the global mass matrices
+ * of Section 2 in tensor products as in Section 4; the c-term of L with c = 1).
+ * With it, one implicit Euler step of calC u' + L u = b,
+ * (calC + tau L) u_new = calC u + tau b, is a solve with a plan whose
+ * coefficients are (tau a_i, 1 + tau c): calC + tau L has the form of L.
+ * Layout and errors as fem_fft_apply; d_u != d_b.  Asynchronous on stream.
+ */
+int fem_fft_apply_mass(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrhs, void* stream);
+
 /* Refinement controls of the MIXED precision (ignored in FP64). */
 int fem_fft_set_refinement(fem_fft_plan plan, double rtol, int max_iter);
 

@@ -172,6 +172,23 @@ def term_apply(prob, u, i):
     return t[0] if single else t
 
 
+def mass_apply(prob, u):
+    """(prod_j calC_j) u: the mass operator of the N-D space (Section 2, the
+    global 1D mass matrices, in tensor products as in Section 4), by
+    axis-wise products with the assembled 1D matrices."""
+    return term_apply(prob, u, prob.N)
+
+
+def heat_step(prob, u, b, tau):
+    """One implicit Euler step of the time-dependent problem C u' + L u = b,
+    C = prod_j calC_j: (C + tau L) u_new = C u + tau b.  C + tau L has the form
+    of L with a_i -> tau a_i and c -> 1 + tau c, so the step is a solve of that
+    scaled problem (algorithm (a) with denominators 1 + tau (sum_i a_i 4 h_i^-2
+    lambda_i + c))."""
+    scaled = Problem(prob.n, prob.K, prob.X, [tau * a for a in prob.a], 1.0 + tau * prob.c)
+    return solve(scaled, mass_apply(prob, u) + tau * np.asarray(b, dtype=np.float64))
+
+
 def grad(prob, f, gu):
     """Gradients of a scalar loss through u = L^{-1} f, given gu = dloss/du.
 

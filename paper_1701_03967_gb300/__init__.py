@@ -16,7 +16,7 @@ import ctypes
 from . import _lib
 from ._lib import FEM_FFT_FP64, FEM_FFT_MIXED, FemFftError  # noqa: F401
 
-__all__ = ["Plan", "Batch", "FemFftError", "solve", "lib_path", "fem_solve"]
+__all__ = ["Plan", "Batch", "HeatStepper", "FemFftError", "solve", "lib_path", "fem_solve"]
 
 lib_path = _lib.LIB_PATH
 
@@ -102,6 +102,14 @@ class Plan:
         b = self._out(u, out)
         _lib.check(_lib.lib().fem_fft_apply(self._h, u.data_ptr(), b.data_ptr(), nrhs, self._stream(stream)),
                    "fem_fft_apply")
+        return b
+
+    def apply_mass(self, u, out=None, stream=None):
+        """b = (C_1 (x) ... (x) C_N) u (float64, matrix-free mass operator)."""
+        nrhs = self._field(u, "u")
+        b = self._out(u, out)
+        _lib.check(_lib.lib().fem_fft_apply_mass(self._h, u.data_ptr(), b.data_ptr(), nrhs, self._stream(stream)),
+                   "fem_fft_apply_mass")
         return b
 
     def forward(self, y, out=None, stream=None):
@@ -308,6 +316,29 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class HeatStepper:
+    """Implicit Euler steps of C u' + L u = b (C the N-D mass operator, L the
+    operator of ``Plan``): (C + tau L) u_new = C u + tau b.  C + tau L has the
+    form of L with a_i -> tau a_i and c -> 1 + tau c, so a step is the mass
+    apply of u plus one solve of that scaled operator (denominators
+    1 + tau (sum_i a_i 4 h_i^-2 lambda_i + c))."""
+
+    def __init__(self, n, K, X=None, a=None, c=0.0, tau=1e-3, precision="fp64", max_nrhs=1, stream=None):
+        N = len(K)
+        a = tuple(float(x) for x in (a if a is not None else (1.0,) * N))
+        self.tau = float(tau)
+        self.plan = Plan(n, K, X, tuple(self.tau * x for x in a), 1.0 + self.tau * float(c), precision,
+                         max_nrhs=max_nrhs, stream=stream)
+
+    def step(self, u, b, out=None, stream=None):
+        rhs = self.plan.apply_mass(u, stream=stream)
+        rhs.add_(b, alpha=self.tau)
+        return self.plan.solve(rhs, out=out, stream=stream)
+
+    def close(self):
+        self.plan.close()
 
 
 def batch_order(nsteps, work=None):

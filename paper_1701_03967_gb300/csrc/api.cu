@@ -90,6 +90,11 @@ int tile_pitch(int K, int Q, int V, int W, bool strided, int elem_bytes) {
 }
 
 void set_fft_passes(PassParams& P) {
+  P.kshift = -1;
+  if (P.ax.K >= 2 && (P.ax.K & (P.ax.K - 1)) == 0) {
+    P.kshift = 0;
+    while ((1 << P.kshift) < P.ax.K) ++P.kshift;
+  }
   int prod = 1;
   for (int ps = 0; ps < kMaxRadixPasses; ++ps) {
     if (ps < P.npass) {
@@ -554,6 +559,26 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
   return FEM_FFT_OK;
 }
 
+// out = (prod_i calC_i) u: one mass application per axis, through the
+// temporaries (float64).
+int mass_chain(fem_fft_plan p, const double* u, long long nrhs, double* out, cudaStream_t s) {
+  const int N = p->N, n1 = p->n + 1;
+  const double* cur = u;
+  int e;
+  for (int ax = 0; ax < N; ++ax) {
+    ApplyParams P = apply_base(p, ax, nrhs);
+    P.in[0] = cur;
+    P.nterm = 1;
+    P.nout = 1;
+    double* dst = ax == N - 1 ? out : p->tmp[ax % 2];
+    P.out[0] = dst;
+    set_mat(P, 0, p->Cref, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+    cur = dst;
+  }
+  return FEM_FFT_OK;
+}
+
 // dots[i] += lam^T (dL/da_i) u (i < N), dots[N] += lam^T (dL/dc) u
 int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrhs, double* dots, cudaStream_t s) {
   const int N = p->N, n1 = p->n + 1;
@@ -938,6 +963,18 @@ int fem_fft_apply(fem_fft_plan p, const double* u, double* b, int64_t nrhs, void
     if ((rc = operator_chain(p, u + (size_t)r0 * p->dof, cnt, 0, b + (size_t)r0 * p->dof, nullptr, nullptr,
                              nullptr, s)))
       return rc;
+  }
+  return FEM_FFT_OK;
+}
+
+int fem_fft_apply_mass(fem_fft_plan p, const double* u, double* b, int64_t nrhs, void* stream) {
+  if (p && nrhs == 0) return FEM_FFT_OK;
+  if (!p || !u || !b || u == b || nrhs < 0) return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  for (int64_t r0 = 0; r0 < nrhs; r0 += p->max_nrhs) {
+    const long long cnt = std::min<int64_t>(p->max_nrhs, nrhs - r0);
+    if ((rc = mass_chain(p, u + (size_t)r0 * p->dof, cnt, b + (size_t)r0 * p->dof, s))) return rc;
   }
   return FEM_FFT_OK;
 }

@@ -108,8 +108,21 @@ struct PassParams {
   int pprod[kMaxRadixPasses];
   int pmask[kMaxRadixPasses];
   int pstride[kMaxRadixPasses];
+  int kshift;        // log2 K when K is a power of two, else -1 (set_fft_passes)
   int in_f64, out_f64, accum;
 };
+
+// c = q * d + r for the divisors K and K / 2 of the pass, by shifts when K
+// is a power of two
+__device__ __forceinline__ void divmod_pow(int c, int d, int shift, int& q, int& r) {
+  if (shift >= 0) {
+    q = c >> shift;
+    r = c & (d - 1);
+  } else {
+    q = c / d;
+    r = c - q * d;
+  }
+}
 
 // ------------------------------------------------------------- radix DFTs
 // forward DFT, omega = exp(-2 pi i / R)
@@ -403,7 +416,8 @@ __device__ void build_sequences(cpx<T>* sm, const PassParams& P) {
     int c = threadIdx.x + t * blockDim.x;
     xl[t] = T(0);
     if (c < nchunks) {
-      int p = c / K, e = c - p * K;
+      int p, e;
+      divmod_pow(c, K, P.kshift, p, e);
       const T* smr = reinterpret_cast<const T*>(sm + p * P.pitch);
       if (e > 0) xl[t] = smr[2 * cofs(e - 1, Q) + (NORD - 1)];
     }
@@ -413,7 +427,8 @@ __device__ void build_sequences(cpx<T>* sm, const PassParams& P) {
   for (int t = 0; t < kMaxChunkTasks; ++t) {
     int c = threadIdx.x + t * blockDim.x;
     if (c < nchunks) {
-      int p = c / K, e = c - p * K;
+      int p, e;
+      divmod_pow(c, K, P.kshift, p, e);
       T* smr = reinterpret_cast<T*>(sm + p * P.pitch) + 2 * cofs(e, Q);
       T y[NORD];
       {
@@ -452,7 +467,8 @@ __device__ void reconstruct(cpx<T>* sm, const PassParams& P) {
   const int K = P.ax.K;
   const int nchunks = P.g.W * K;
   for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
-    int p = c / K, e = c - p * K;
+    int p, e;
+    divmod_pow(c, K, P.kshift, p, e);
     cpx<T>* ch = sm + p * P.pitch + cofs(e, Q);
     cpx<T> x[Q];
 #pragma unroll
@@ -514,10 +530,11 @@ __device__ void post_twiddle(cpx<T>* sm, const PassParams& P, const cpx<T>* rot)
   const int npairs = K / 2;
   const int ntask = P.g.W * npairs * Q;
   for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-    const int q = task % Q;
     const int r = task / Q;
-    const int k = 1 + r % npairs;
-    const int p = r / npairs;
+    const int q = task - r * Q;
+    int p, km1;
+    divmod_pow(r, npairs, P.kshift - 1, p, km1);
+    const int k = 1 + km1;
     cpx<T>* pen = sm + p * P.pitch;
     const int kk = K - k;
     const cpx<T> rk = rot[k];
@@ -669,10 +686,11 @@ __device__ void pre_twiddle(cpx<T>* sm, const PassParams& P, const cpx<T>* rot) 
   const int npairs = K / 2;
   const int ntask = P.g.W * npairs * Q;
   for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
-    const int q = task % Q;
     const int r = task / Q;
-    const int k = 1 + r % npairs;
-    const int p = r / npairs;
+    const int q = task - r * Q;
+    int p, km1;
+    divmod_pow(r, npairs, P.kshift - 1, p, km1);
+    const int k = 1 + km1;
     cpx<T>* pen = sm + p * P.pitch;
     const int kk = K - k;
     const cpx<T> rk = rot[k];

@@ -196,3 +196,26 @@ def test_mixed_residual_precisions(case):
         out[mode] = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
         assert _rel(out[mode], want) <= 1e-10, (mode, _rel(out[mode], want))
     assert _rel(out["df64"], out["f64"]) <= 1e-11
+
+
+@pytest.mark.parametrize("case", [dict(n=3, K=(8, 12), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
+                                  dict(n=2, K=(8, 6, 8), a=(1.0, 2.0, 0.5), c=0.3)], ids=["2d", "3d"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_mass_apply_and_heat_steps(case, precision, tol):
+    """The mass operator and five implicit Euler steps of C u' + L u = b
+    against the oracle's heat step."""
+    from paper_1701_03967_gb300 import HeatStepper
+    prob = _prob(case)
+    u0 = synth.normal_batch(2, prob.M, synth.CFG_TEST, 21)
+    b = synth.normal_batch(2, prob.M, synth.CFG_TEST, 22)
+    tau = 0.02
+    st = HeatStepper(case["n"], case["K"], case.get("X"), case.get("a"), case.get("c", 0.0), tau, precision,
+                     max_nrhs=2)
+    ut, bt = torch.from_numpy(u0).cuda(), torch.from_numpy(b).cuda()
+    assert _rel(st.plan.apply_mass(ut).cpu().numpy(), osolve.mass_apply(prob, u0)) <= 1e-13
+    want = u0
+    for _ in range(5):
+        ut = st.step(ut, bt)
+        want = osolve.heat_step(prob, want, b, tau)
+    assert _rel(ut.cpu().numpy(), want) <= tol
+    st.close()

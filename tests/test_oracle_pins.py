@@ -13,6 +13,7 @@ import os
 from fractions import Fraction
 
 import numpy as np
+import scipy.linalg
 import pytest
 
 from oracle import fem1d, harness, solve
@@ -181,6 +182,45 @@ def test_solve_matches_brute_force_dense_solve(case):
     # apply = L u
     np.testing.assert_allclose(solve.apply(p, want).reshape(2, -1),
                                (L @ want.reshape(2, -1).T).T, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("case", CASES[:5])
+def test_heat_step_matches_dense_implicit_euler(case):
+    """One implicit Euler step of C u' + L u = b (C the N-D mass operator):
+    (C + tau L) u_new = C u + tau b, against dense Kronecker products of the
+    assembled 1D matrices and a dense solve."""
+    p = solve.Problem(case["n"], case["K"], case["X"], case["a"], case["c"])
+    u = synth.normal_batch(2, p.M, synth.CFG_TEST, 11)
+    b = synth.normal_batch(2, p.M, synth.CFG_TEST, 12)
+    tau = 0.013
+    C = np.ones((1, 1))
+    for i in range(p.N):
+        C = np.kron(C, fem1d.assemble(p.n, p.K[i])[1])
+    L = solve.assemble_dense(p)
+    rhs = (C @ u.reshape(2, -1).T + tau * b.reshape(2, -1).T)
+    want = np.linalg.solve(C + tau * L, rhs).T.reshape(u.shape)
+    got = solve.heat_step(p, u, b, tau)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
+    np.testing.assert_allclose(solve.mass_apply(p, u).reshape(2, -1), (C @ u.reshape(2, -1).T).T,
+                               rtol=1e-12, atol=1e-13)
+
+
+def test_heat_step_decays_eigenmodes_exactly():
+    """A product of 1D generalized eigenvectors (calA v = lambda calC v, from
+    LAPACK) decays in one step with b = 0 by exactly
+    1 / (1 + tau (sum_i a_i 4 h_i^-2 lambda_i + c))."""
+    p = solve.Problem(3, (5, 4), (1.0, 2.0), (1.3, 0.6), 0.7)
+    tau = 0.05
+    vecs, lams = [], []
+    for i, pick in enumerate((2, 7)):
+        calA, calC = fem1d.assemble(p.n, p.K[i])
+        w, V = scipy.linalg.eigh(calA, calC)
+        vecs.append(V[:, pick])
+        lams.append(w[pick])
+    u = np.multiply.outer(vecs[0], vecs[1])
+    got = solve.heat_step(p, u, np.zeros_like(u), tau)
+    factor = 1.0 / (1.0 + tau * (sum(p.a[i] * p.s[i] * lams[i] for i in range(2)) + p.c))
+    np.testing.assert_allclose(got, factor * u, rtol=1e-11, atol=1e-13)
 
 
 def test_paper_error_tables():
