@@ -23,7 +23,7 @@ def _grads(plan, f, ut, a, c):
     u = fem_solve(plan, ft, at, ct)
     loss = torch.sum((u - torch.from_numpy(ut).cuda()) ** 2)
     loss.backward()
-    return float(loss), ft.grad.cpu().numpy(), at.grad.numpy(), float(ct.grad)
+    return float(loss.detach()), ft.grad.cpu().numpy(), at.grad.numpy(), float(ct.grad)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
