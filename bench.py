@@ -133,8 +133,8 @@ def time_steps(torch, fn, steps, warmup, barrier=None):
 
 # DRAM bytes (read + write) per DOF of one double-float residual apply, the
 # average of the three launches of a 2D n=9 residual chain, from ncu
-# (profiles/apply_kernel_df_2d_n9_K512.md: 510.7 MB per launch at 21.2 M DOF)
-APPLY_DF_TRAFFIC_PER_DOF_2D_N9 = 510.7e6 / 21224449
+# (profiles/apply_kernel_df_2d_n9_K512.md: 573.2 MB per launch at 21.2 M DOF)
+APPLY_DF_TRAFFIC_PER_DOF_2D_N9 = 573.2e6 / 21224449
 
 
 def roofline(prof, steps, peaks, wl=None):
@@ -250,6 +250,7 @@ def run_other_workloads(torch, args, barrier):
         ref = None
         for prec in ("mixed", "fp64"):
             pl = Plan(n, K, X, a, c, precision=prec)
+            pl.tune()
             b = torch.randn(pl.M, dtype=torch.float64, device="cuda", generator=g) if ref is None else ref[0]
             u = torch.empty_like(b)
             ms = time_steps(torch, lambda: pl.solve(b, out=u), steps, args.warmup, barrier)
@@ -382,6 +383,9 @@ def main():
     mixed = Plan(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"], precision="mixed")
     mixed.set_refinement(0.0, args.refine)
     fp64 = Plan(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"], precision="fp64")
+    # launch shapes of both plans tuned on the device (plan setup, untimed)
+    mixed.tune()
+    fp64.tune()
     b_host = synth.normal_field(mixed.M, cfg_id, 0, rank)
     b = torch.from_numpy(b_host).to(f"cuda:{dev}")
     u = torch.empty_like(b)

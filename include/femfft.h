@@ -135,6 +135,17 @@ int fem_fft_apply(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrh
  */
 int fem_fft_apply_mass(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrhs, void* stream);
 
+/*
+ * fem_fft_plan_tune -- time the plan's pencil passes (the launches of
+ * fem_fft_solve, on the plan's own zeroed workspace) for every admissible
+ * tile shape (pencils per CTA, powers of two) and FFT values per thread
+ * (4, 8 or 6, 12), and keep the fastest per pass for later solves.  No paper
+ * counterpart (a launch-configuration tuner).  Synchronises stream; about a
+ * second for large plans.  Results are exact-arithmetic neutral: every
+ * shape computes the same transforms.
+ */
+int fem_fft_plan_tune(fem_fft_plan plan, void* stream);
+
 /* Refinement controls of the MIXED precision (ignored in FP64). */
 int fem_fft_set_refinement(fem_fft_plan plan, double rtol, int max_iter);
 

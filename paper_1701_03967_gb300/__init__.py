@@ -136,6 +136,11 @@ class Plan:
                    "fem_fft_plan_set_coefficients")
         self.a, self.c = a, float(c)
 
+    def tune(self, stream=None):
+        """Time the plan's pencil passes over tile shapes and FFT schedules and
+        keep the fastest (fem_fft_plan_tune)."""
+        _lib.check(_lib.lib().fem_fft_plan_tune(self._h, self._stream(stream)), "fem_fft_plan_tune")
+
     def set_residual_precision(self, mode="df64"):
         """Arithmetic of the refinement residual of a mixed plan: "df64"
         (double-float on the float pipes, default) or "f64"."""

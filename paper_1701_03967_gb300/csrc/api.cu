@@ -250,6 +250,23 @@ int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inn
       tiles = outer * ((inner + W - 1) / W);
     }
   }
+  // tuned shape (fem_fft_plan_tune), clipped to what this pass admits
+  const fem_fft_plan_s::Tuned& tu = p->tuned[mode][axis][f64 ? 1 : 0];
+  if (tu.W > 0) {
+    int np, rad[kMaxRadixPasses];
+    if (fft_schedule_v(K, tu.V, &np, rad) && K / tu.V <= threads) {
+      P.V = tu.V;
+      P.npass = np;
+      for (int i = 0; i < kMaxRadixPasses; ++i) P.radix[i] = i < np ? rad[i] : 0;
+    }
+    long long w = std::min<long long>(tu.W, wmax);
+    if (inner > 1) {
+      long long p2 = 1;
+      while (p2 * 2 <= std::min(w, inner)) p2 *= 2;
+      w = p2;
+    }
+    W = std::max<long long>(1, w);
+  }
   P.g.outer = outer;
   P.g.inner = inner;
   P.g.M = M;
@@ -977,6 +994,72 @@ int fem_fft_apply_mass(fem_fft_plan p, const double* u, double* b, int64_t nrhs,
     if ((rc = mass_chain(p, u + (size_t)r0 * p->dof, cnt, b + (size_t)r0 * p->dof, s))) return rc;
   }
   return FEM_FFT_OK;
+}
+
+int fem_fft_plan_tune(fem_fft_plan p, void* stream) {
+  if (!p) return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f64 = p->precision == FEM_FFT_FP64;
+  // scratch: the plan's own workspace, zeroed (contents do not affect timing)
+  void* buf = f64 ? (void*)p->tmp[0] : (void*)p->w32;
+  const size_t bytes = (size_t)p->max_nrhs * p->dof * (f64 ? sizeof(double) : sizeof(float));
+  if (!buf) return FEM_FFT_OK;   // 1D FP64 plans have no temporary: nothing to tune against
+  FEMFFT_CUDA(cudaMemsetAsync(buf, 0, bytes, s), "tune scratch");
+  cudaEvent_t e0, e1;
+  FEMFFT_CUDA(cudaEventCreate(&e0), "tune events");
+  FEMFFT_CUDA(cudaEventCreate(&e1), "tune events");
+  const bool was_profiling = p->profiling;
+  p->profiling = false;
+  int rc = FEM_FFT_OK;
+  const int threads = f64 ? kPencilThreads64 : kPencilThreads;
+  struct Pass { int mode, axis; };
+  std::vector<Pass> passes;
+  for (int ax = p->N - 1; ax >= 1; --ax) passes.push_back({MODE_FWD, ax});
+  passes.push_back({MODE_FUSED, 0});
+  for (int ax = 1; ax < p->N; ++ax) passes.push_back({MODE_INV, ax});
+  for (const Pass& ps : passes) {
+    fem_fft_plan_s::Tuned& tu = p->tuned[ps.mode][ps.axis][f64 ? 1 : 0];
+    const int K = (int)p->K[ps.axis];
+    fem_fft_plan_s::Tuned best;
+    float best_ms = 1e30f;
+    for (int V : {4, 8, 6, 12}) {
+      int np, rad[kMaxRadixPasses];
+      if (!fft_schedule_v(K, V, &np, rad) || K / V > threads) continue;
+      for (int W = 1; W <= (f64 ? kMaxW64 : kMaxW); W *= 2) {
+        tu.W = W;
+        tu.V = V;
+        // the candidate must keep its shape after clipping
+        long long outer = p->max_nrhs, inner = 1;
+        for (int j = 0; j < ps.axis; ++j) outer *= p->M[j];
+        for (int j = ps.axis + 1; j < p->N; ++j) inner *= p->M[j];
+        PassPlan pp;
+        if (plan_pass(p, ps.mode, ps.axis, outer, inner, f64, &pp) || pp.P.g.W != W || pp.P.V != V) continue;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && !rc; ++rep) {
+          cudaEventRecord(e0, s);
+          rc = run_pass(p, ps.mode, ps.axis, p->max_nrhs, f64, buf, f64, buf, f64, false, s);
+          cudaEventRecord(e1, s);
+          if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = FEM_FFT_ERR_CUDA;
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          if (rep > 0) ms = std::min(ms, t);
+        }
+        if (rc) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best.W = W;
+          best.V = V;
+        }
+      }
+      if (rc) break;
+    }
+    tu = best;   // W = 0 (heuristic) if no candidate ran
+    if (rc) break;
+  }
+  p->profiling = was_profiling;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 int fem_fft_forward(fem_fft_plan p, const double* y, double* c, int64_t nrhs, void* stream) {

@@ -89,6 +89,12 @@ struct fem_fft_plan_s {
   std::vector<void*> allocs;
   // when set, pencil passes and applies are appended here instead of launched
   std::vector<femfft::RecordedOp>* rec = nullptr;
+  // tile shape (pencils per CTA W) and FFT values per thread V chosen by
+  // fem_fft_plan_tune per [mode][axis][float64]; W = 0: the default heuristic
+  struct Tuned {
+    int W = 0, V = 0;
+  };
+  Tuned tuned[3][femfft::kMaxN][2];
   // kernel timing (fem_fft_profile)
   struct ProfRec {
     cudaEvent_t a, b;

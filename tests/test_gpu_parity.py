@@ -219,3 +219,17 @@ def test_mass_apply_and_heat_steps(case, precision, tol):
         want = osolve.heat_step(prob, want, b, tau)
     assert _rel(ut.cpu().numpy(), want) <= tol
     st.close()
+
+
+@pytest.mark.parametrize("case", [dict(n=9, K=(16, 32), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
+                                  dict(n=4, K=(8, 12, 8), a=(1.0, 2.0, 0.5), c=0.3)], ids=["2d_n9", "3d_n4"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_tuned_plan_matches_oracle(case, precision, tol):
+    """fem_fft_plan_tune changes only launch shapes: the tuned plan still
+    matches the oracle."""
+    prob = _prob(case)
+    b = synth.normal_batch(2, prob.M, synth.CFG_TEST, 31)
+    plan = _plan(case, precision, max_nrhs=2)
+    plan.tune()
+    got = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert _rel(got, osolve.solve(prob, b)) <= tol
