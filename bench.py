@@ -239,18 +239,20 @@ def run_other_workloads(torch, args, barrier):
     """The other configurations, timed like the headline (device-resident
     N(0,1) right-hand sides, CUDA events): the n = 1..9 sweep of the 2D
     workload at K = 1024 x 1024, the 3D workloads n=9 K=64^3 and n=4 K=128^3
-    (mixed and FP64), and one differentiation step (forward solve + adjoint
-    solve + coefficient gradients) of 3D n=5 K=64^3 in mixed precision."""
+    (mixed and FP64), algorithm (b) on the 2D n=9 and 3D n=9 workloads, and
+    one differentiation step (forward solve + adjoint solve + coefficient
+    gradients) of 3D n=5 K=64^3 in mixed precision."""
     from paper_1701_03967_gb300 import Plan, fem_solve
     g = torch.Generator(device="cuda").manual_seed(1701)
     steps = max(2, args.steps // 2)
 
-    def pair(n, K, X, a, c):
+    def pair(n, K, X, a, c, algo="a"):
         out = {}
         ref = None
         for prec in ("mixed", "fp64"):
             pl = Plan(n, K, X, a, c, precision=prec)
             pl.tune()
+            pl.set_algorithm(algo)
             b = torch.randn(pl.M, dtype=torch.float64, device="cuda", generator=g) if ref is None else ref[0]
             u = torch.empty_like(b)
             ms = time_steps(torch, lambda: pl.solve(b, out=u), steps, args.warmup, barrier)
@@ -270,6 +272,11 @@ def run_other_workloads(torch, args, barrier):
     res["3d_n9_K64"] = pair(9, (64, 64, 64), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.0)
     torch.cuda.empty_cache()
     res["3d_n4_K128"] = pair(4, (128, 128, 128), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.0)
+    torch.cuda.empty_cache()
+    # algorithm (b): transforms along x_2..x_N, band solves along x_1
+    res["algo_b_2d_n9_K1024"] = pair(9, (1024, 1024), (1.0, 2.0), (1.0, 2.5), 1.0, algo="b")
+    torch.cuda.empty_cache()
+    res["algo_b_3d_n9_K64"] = pair(9, (64, 64, 64), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.0, algo="b")
     torch.cuda.empty_cache()
     pl = Plan(5, (64, 64, 64), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.0, precision="mixed")
     f = torch.randn(pl.M, dtype=torch.float64, device="cuda", generator=g).requires_grad_(True)

@@ -136,6 +136,23 @@ int fem_fft_apply(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrh
 int fem_fft_apply_mass(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrhs, void* stream);
 
 /*
+ * fem_fft_set_algorithm -- the solver of fem_fft_solve (N >= 2):
+ * FEM_FFT_ALGO_A (default) is algorithm (a) of Section 4 (FC_n / F_n
+ * transforms along every axis and the spectral division); FEM_FFT_ALGO_B is
+ * algorithm (b): the transforms along x_2..x_N only and, for every position
+ * of those axes, the 1D problem [a_1 4 h_1^-2 calA_1 + (sum_{i>=2} a_i
+ * 4 h_i^-2 lambda_i + c) calC_1] v = f~ along x_1, a symmetric positive
+ * definite band system solved by static condensation of the element
+ * interiors and a tridiagonal vertex solve.  Both give the solution of
+ * L u = b.  Setting B computes its tables (one row of n + 2 values per
+ * position of x_2..x_N) and a scratch of max_nrhs * (K_1 - 1) * M_2..M_N
+ * values; synchronises stream.  FEM_FFT_ERR_ARG for N = 1 or with batches
+ * (a plan set to B cannot join fem_fft_batch_create).
+ */
+enum { FEM_FFT_ALGO_A = 0, FEM_FFT_ALGO_B = 1 };
+int fem_fft_set_algorithm(fem_fft_plan plan, int algo, void* stream);
+
+/*
  * fem_fft_plan_tune -- time the plan's pencil passes (the launches of
  * fem_fft_solve, on the plan's own zeroed workspace) for every admissible
  * tile shape (pencils per CTA, powers of two) and FFT values per thread

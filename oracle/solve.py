@@ -172,6 +172,45 @@ def term_apply(prob, u, i):
     return t[0] if single else t
 
 
+def solve_b(prob, b):
+    """u = L^{-1} b by algorithm (b) of Section 4: the direct FC_n-expansion
+    in x_2..x_N only, then for every spectral index (k_2 l_2, ..., k_N l_N)
+    the 1D problem in x_1
+        [a_1 4 h_1^-2 calA_1 + (sum_{i>=2} a_i 4 h_i^-2 lambda_i + c) calC_1] v = f~
+    solved by banded Cholesky (its matrix is symmetric positive definite with
+    half-bandwidth n), then the inverse F_n-expansion in x_2..x_N."""
+    import scipy.linalg
+    x, single = _as_batch(prob, b)
+    for i in range(1, prob.N):
+        _, S, cn = prob.basis1d(i)
+        x = _axis_apply(x, S.T / cn[:, None], i + 1)
+    # denominators of the later axes (the x_1 term is the banded solve)
+    D = np.full(prob.M[1:], prob.c, dtype=np.float64)
+    for i in range(1, prob.N):
+        lam, _, _ = prob.basis1d(i)
+        shape = [1] * (prob.N - 1)
+        shape[i - 1] = prob.M[i]
+        D = D + (prob.a[i] * prob.s[i] * lam).reshape(shape)
+    calA, calC = prob.ops1d(0)
+    n = prob.n
+    alpha = prob.a[0] * prob.s[0]
+    M0 = prob.M[0]
+    y = np.moveaxis(x, 1, -1).reshape(-1, M0)          # (rhs x later spectral, M0)
+    beta = np.broadcast_to(D, x.shape[:1] + D.shape).reshape(-1)
+    out = np.empty_like(y)
+    for r in range(y.shape[0]):
+        Mat = alpha * calA + beta[r] * calC
+        ab = np.zeros((n + 1, M0))                    # upper banded storage
+        for d in range(n + 1):
+            ab[n - d, d:] = np.diagonal(Mat, d)
+        out[r] = scipy.linalg.solveh_banded(ab, y[r])
+    v = np.moveaxis(out.reshape(x.shape[:1] + x.shape[2:] + (M0,)), -1, 1)
+    for i in range(1, prob.N):
+        _, S, _ = prob.basis1d(i)
+        v = _axis_apply(v, S, i + 1)
+    return v[0] if single else v
+
+
 def mass_apply(prob, u):
     """(prod_j calC_j) u: the mass operator of the N-D space (Section 2, the
     global 1D mass matrices, in tensor products as in Section 4), by

@@ -136,6 +136,12 @@ class Plan:
                    "fem_fft_plan_set_coefficients")
         self.a, self.c = a, float(c)
 
+    def set_algorithm(self, algo="a", stream=None):
+        """Solver of ``solve`` (N >= 2): "a" (transforms along every axis,
+        default) or "b" (transforms along x_2..x_N, band solves along x_1)."""
+        code = {"a": 0, "b": 1}[algo]
+        _lib.check(_lib.lib().fem_fft_set_algorithm(self._h, code, self._stream(stream)), "fem_fft_set_algorithm")
+
     def tune(self, stream=None):
         """Time the plan's pencil passes over tile shapes and FFT schedules and
         keep the fastest (fem_fft_plan_tune)."""

@@ -332,6 +332,118 @@ int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const
   return FEM_FFT_OK;
 }
 
+// Algorithm (b) along axis 0, in place on the work array (N >= 2).
+int run_band(fem_fft_plan p, long long nrhs, bool f64, void* work, cudaStream_t s) {
+  if (p->rec) {
+    set_last_error("algorithm (b) has no batched form");
+    return FEM_FFT_ERR_ARG;
+  }
+  BandParams B = p->band_proto;
+  B.f = work;
+  B.tab = f64 ? p->band_tab64 : p->band_tab32;
+  B.scr = p->band_scr;
+  B.outer = nrhs;
+  const double elems = (double)nrhs * p->dof;
+  // bytes of the three phases: field read + written twice, vertex rows twice
+  const double bytes = elems * (f64 ? 8.0 : 4.0) * (4.0 + 4.0 / p->n);
+  int e;
+  {
+    ProfScope scope(p, s, 1, bytes, 0.0);
+    e = launch_band(B, f64, s);
+  }
+  if (e) return cuda_fail((cudaError_t)e, "band solve launch");
+  return FEM_FFT_OK;
+}
+
+// Tables of algorithm (b): for every position w of the later axes
+// beta_w = c + sum_{i>=1} a_i s_i lambda_i, r_m = 1 / (alpha nu_m + beta_w) and
+// the vertex system D = S_00 + S_11, off = S_01 of the element Schur
+// complement; element data from the interior eigenpairs of the reference
+// matrices.
+int build_band_tables(fem_fft_plan p, cudaStream_t s) {
+  const int n = p->n, n1 = n + 1, NI = n - 1;
+  std::vector<double> nu, phi;
+  if (interior_eig(n, &nu, &phi)) return FEM_FFT_ERR_ASSUMPTION_A;
+  BandParams& B = p->band_proto;
+  std::memset(&B, 0, sizeof(B));
+  B.M = (int)p->M[0];
+  B.K = (int)p->K[0];
+  B.n = n;
+  B.alpha = p->a[0] * 4.0 * p->K[0] * p->K[0] / (p->X[0] * p->X[0]);
+  long long inner = 1;
+  for (int j = 1; j < p->N; ++j) inner *= p->M[j];
+  B.inner = inner;
+  const std::vector<double>& A = p->Aref;
+  const std::vector<double>& C = p->Cref;
+  const int bi[2] = {0, n};
+  for (int i = 0; i < NI * NI; ++i) {
+    B.phi[i] = phi[i];
+    B.phif[i] = (float)phi[i];
+  }
+  std::vector<double> pta(NI * 2), ptc(NI * 2);
+  for (int l = 0; l < NI; ++l)
+    for (int b = 0; b < 2; ++b) {
+      double sa = 0.0, sc = 0.0;
+      for (int i = 0; i < NI; ++i) {
+        sa += phi[i * NI + l] * A[(i + 1) * n1 + bi[b]];
+        sc += phi[i * NI + l] * C[(i + 1) * n1 + bi[b]];
+      }
+      pta[l * 2 + b] = sa;
+      ptc[l * 2 + b] = sc;
+      B.pta[l][b] = sa;
+      B.ptc[l][b] = sc;
+      B.ptaf[l][b] = (float)sa;
+      B.ptcf[l][b] = (float)sc;
+    }
+  for (int b = 0; b < 2; ++b)
+    for (int m = 0; m < NI; ++m) {
+      B.abi[b][m] = A[bi[b] * n1 + (m + 1)];
+      B.cbi[b][m] = C[bi[b] * n1 + (m + 1)];
+      B.abif[b][m] = (float)B.abi[b][m];
+      B.cbif[b][m] = (float)B.cbi[b][m];
+    }
+  // per position of the later axes
+  const int RB = n + 2;
+  std::vector<double> tab((size_t)inner * RB);
+  for (long long w = 0; w < inner; ++w) {
+    double beta = p->c;
+    long long rem = w;
+    for (int j = p->N - 1; j >= 1; --j) {
+      const long long idx = rem % p->M[j];
+      rem /= p->M[j];
+      beta += p->ax[j].mu[idx];
+    }
+    double* t = &tab[(size_t)w * RB];
+    t[0] = beta;
+    double S[2][2];
+    for (int x = 0; x < 2; ++x)
+      for (int y = 0; y < 2; ++y) S[x][y] = B.alpha * A[bi[x] * n1 + bi[y]] + beta * C[bi[x] * n1 + bi[y]];
+    for (int m = 0; m < NI; ++m) {
+      const double r = 1.0 / (B.alpha * nu[m] + beta);
+      t[1 + m] = r;
+      const double e0 = B.alpha * pta[m * 2] + beta * ptc[m * 2];
+      const double e1 = B.alpha * pta[m * 2 + 1] + beta * ptc[m * 2 + 1];
+      S[0][0] -= e0 * r * e0;
+      S[0][1] -= e0 * r * e1;
+      S[1][1] -= e1 * r * e1;
+    }
+    t[n] = S[0][0] + S[1][1];
+    t[n + 1] = S[0][1];
+  }
+  int rc;
+  if (!p->band_tab64 && (rc = dev_alloc(p, &p->band_tab64, tab.size() * sizeof(double)))) return rc;
+  if (!p->band_tab32 && (rc = dev_alloc(p, &p->band_tab32, tab.size() * sizeof(float)))) return rc;
+  const size_t scr_elems = (size_t)p->max_nrhs * inner * (p->K[0] - 1);
+  if (!p->band_scr && (rc = dev_alloc(p, &p->band_scr, std::max<size_t>(1, scr_elems) * sizeof(double)))) return rc;
+  std::vector<float> tab32(tab.begin(), tab.end());
+  FEMFFT_CUDA(cudaMemcpyAsync(p->band_tab64, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s),
+              "band tables");
+  FEMFFT_CUDA(cudaMemcpyAsync(p->band_tab32, tab32.data(), tab32.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+              "band tables");
+  FEMFFT_CUDA(cudaStreamSynchronize(s), "band tables");
+  return FEM_FFT_OK;
+}
+
 // Algorithm (a): forward passes on axes N-1..1, fused forward/divide/inverse
 // on axis 0, inverse passes on axes 1..N-1.
 int solve_chain(fem_fft_plan p, bool f64, const void* in, bool in_f64, void* work, void* out, bool accum,
@@ -347,7 +459,12 @@ int solve_chain(fem_fft_plan p, bool f64, const void* in, bool in_f64, void* wor
   }
   // fused pass: the last pass of the chain when N == 1
   if (N == 1) return run_pass(p, MODE_FUSED, 0, nrhs, f64, cur, cur_f64, out, true, accum, s);
-  if ((rc = run_pass(p, MODE_FUSED, 0, nrhs, f64, cur, cur_f64, work, f64, false, s))) return rc;
+  if (p->algo == 1) {
+    // algorithm (b): banded solves along x_1 in place of the transforms there
+    if ((rc = run_band(p, nrhs, f64, work, s))) return rc;
+  } else if ((rc = run_pass(p, MODE_FUSED, 0, nrhs, f64, cur, cur_f64, work, f64, false, s))) {
+    return rc;
+  }
   for (int ax = 1; ax < N; ++ax) {
     bool last = ax == N - 1;
     if ((rc = run_pass(p, MODE_INV, ax, nrhs, f64, work, f64, last ? out : work, last ? true : f64,
@@ -840,6 +957,7 @@ int fem_fft_plan_set_coefficients(fem_fft_plan p, const double* h_a, double c, v
     p->a[i] = h_a[i];
   }
   p->c = c;
+  if (p->algo == 1) return build_band_tables(p, s);
   return FEM_FFT_OK;
 }
 
@@ -993,6 +1111,20 @@ int fem_fft_apply_mass(fem_fft_plan p, const double* u, double* b, int64_t nrhs,
     const long long cnt = std::min<int64_t>(p->max_nrhs, nrhs - r0);
     if ((rc = mass_chain(p, u + (size_t)r0 * p->dof, cnt, b + (size_t)r0 * p->dof, s))) return rc;
   }
+  return FEM_FFT_OK;
+}
+
+int fem_fft_set_algorithm(fem_fft_plan p, int algo, void* stream) {
+  if (!p || (algo != FEM_FFT_ALGO_A && algo != FEM_FFT_ALGO_B)) return FEM_FFT_ERR_ARG;
+  if (algo == FEM_FFT_ALGO_B) {
+    if (p->N < 2) {
+      g_last_error = "algorithm (b) needs N >= 2 (for N = 1 it is a single banded solve)";
+      return FEM_FFT_ERR_ARG;
+    }
+    int rc = build_band_tables(p, (cudaStream_t)stream);
+    if (rc) return rc;
+  }
+  p->algo = algo == FEM_FFT_ALGO_B ? 1 : 0;
   return FEM_FFT_OK;
 }
 

@@ -1,0 +1,240 @@
+// Algorithm (b) of Section 4 along axis 0: after the direct FC_n-transforms
+// in the later axes, every position w of those axes carries an independent
+// 1D problem [alpha calA + beta_w calC] v = y in x_1 (alpha = a_1 4 h_1^-2,
+// beta_w = c + sum_{i>=2} a_i 4 h_i^-2 lambda_i), symmetric positive definite
+// with half-bandwidth n.
+//
+// It is solved by static condensation, which is the banded factorisation
+// ordered element interiors first:
+//  1. per element (parallel): the interior block E_ii = alpha A_ii + beta C_ii
+//     is inverted through the generalized eigenvectors of (A_ii, C_ii) (the
+//     bubble modes of Section 2): E_ii^-1 = Phi diag(r) Phi^T with
+//     r_m = 1 / (alpha nu_m + beta); z = E_ii^-1 y_i replaces the interiors,
+//     the condensed right-hand side y_v - E_bi z is formed for the vertices;
+//  2. per 1D problem (parallel over w): the vertex system is symmetric
+//     tridiagonal with constant coefficients (D = S_00 + S_11, off = S_01 of
+//     the element Schur complement S = E_bb - E_bi E_ii^-1 E_ib) and is solved
+//     by Gaussian elimination without pivoting (Thomas algorithm; stable for
+//     symmetric positive definite matrices);
+//  3. per element (parallel): interiors v_i = z - E_ii^-1 E_ib v_b.
+// Every thread writes only its own element's slots; the right-vertex
+// contribution of element e goes to a scratch row and is added by the
+// vertex solve, so the result does not depend on thread timing.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace femfft {
+
+namespace {
+
+constexpr int kBandThreads = 256;
+
+template <typename T>
+struct ElemData;
+template <>
+struct ElemData<double> {
+  __device__ static double phi(const BandParams& P, int i) { return P.phi[i]; }
+  __device__ static double pta(const BandParams& P, int l, int b) { return P.pta[l][b]; }
+  __device__ static double ptc(const BandParams& P, int l, int b) { return P.ptc[l][b]; }
+  __device__ static double abi(const BandParams& P, int b, int m) { return P.abi[b][m]; }
+  __device__ static double cbi(const BandParams& P, int b, int m) { return P.cbi[b][m]; }
+};
+template <>
+struct ElemData<float> {
+  __device__ static float phi(const BandParams& P, int i) { return P.phif[i]; }
+  __device__ static float pta(const BandParams& P, int l, int b) { return P.ptaf[l][b]; }
+  __device__ static float ptc(const BandParams& P, int l, int b) { return P.ptcf[l][b]; }
+  __device__ static float abi(const BandParams& P, int b, int m) { return P.abif[b][m]; }
+  __device__ static float cbi(const BandParams& P, int b, int m) { return P.cbif[b][m]; }
+};
+
+// block bx -> (outer o, element e, position w); false if out of range
+__device__ __forceinline__ bool band_elem(const BandParams& P, int TW, long long& o, int& e, long long& w) {
+  const int TE = kBandThreads / TW;
+  const long long wtiles = (P.inner + TW - 1) / TW;
+  const long long etiles = (P.K + TE - 1) / TE;
+  long long bx = blockIdx.x;
+  const long long et = bx % etiles;
+  bx /= etiles;
+  const long long wt = bx % wtiles;
+  o = bx / wtiles;
+  w = wt * TW + threadIdx.x % TW;
+  e = (int)(et * TE + threadIdx.x / TW);
+  return w < P.inner && e < P.K;
+}
+
+template <typename T, int NORD>
+__global__ void __launch_bounds__(kBandThreads) band_condense_kernel(BandParams P, int TW) {
+  constexpr int NI = NORD - 1, NI1 = NI > 0 ? NI : 1;
+  using D = ElemData<T>;
+  long long o, w;
+  int e;
+  if (!band_elem(P, TW, o, e, w)) return;
+  T* f = reinterpret_cast<T*>(P.f);
+  T* scr = reinterpret_cast<T*>(P.scr);
+  const long long line = o * (long long)P.M * P.inner + w;
+  const long long npen = P.outer * P.inner, pen = o * P.inner + w;
+  const T* tab = reinterpret_cast<const T*>(P.tab) + w * (NORD + 2);
+  const T beta = tab[0], alpha = T(P.alpha);
+  T gl = T(0), gr = T(0);
+  if (NI > 0) {
+    T y[NI1], s[NI1];
+#pragma unroll
+    for (int m = 0; m < NI; ++m) y[m] = f[line + (long long)(NORD * e + m) * P.inner];
+#pragma unroll
+    for (int l = 0; l < NI; ++l) {
+      T acc = T(0);
+#pragma unroll
+      for (int i = 0; i < NI; ++i) acc = fma(D::phi(P, i * NI + l), y[i], acc);
+      s[l] = acc * tab[1 + l];
+    }
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      T z = T(0);
+#pragma unroll
+      for (int l = 0; l < NI; ++l) z = fma(D::phi(P, i * NI + l), s[l], z);
+      f[line + (long long)(NORD * e + i) * P.inner] = z;
+      gl = fma(alpha * D::abi(P, 0, i) + beta * D::cbi(P, 0, i), z, gl);
+      gr = fma(alpha * D::abi(P, 1, i) + beta * D::cbi(P, 1, i), z, gr);
+    }
+  }
+  if (e >= 1) {
+    const long long v = line + (long long)(NORD * e - 1) * P.inner;   // left vertex of element e
+    f[v] = f[v] - gl;
+  }
+  if (e <= P.K - 2) scr[(long long)e * npen + pen] = -gr;
+}
+
+template <typename T>
+__device__ __forceinline__ T band_recip(T d);
+template <>
+__device__ __forceinline__ float band_recip(float d) { return 1.0f / d; }
+template <>
+__device__ __forceinline__ double band_recip(double d) { return 1.0 / d; }
+
+template <typename T, int NORD>
+__global__ void __launch_bounds__(kBandThreads) band_vertex_kernel(BandParams P) {
+  const long long npen = P.outer * P.inner;
+  const long long pen = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pen >= npen) return;
+  const long long o = pen / P.inner, w = pen - o * P.inner;
+  T* f = reinterpret_cast<T*>(P.f);
+  T* scr = reinterpret_cast<T*>(P.scr);
+  const long long line = o * (long long)P.M * P.inner + w;
+  const T* tab = reinterpret_cast<const T*>(P.tab) + w * (NORD + 2);
+  const T Dg = tab[NORD], off = tab[NORD + 1];
+  const int nv = P.K - 1;   // vertices j = 1..K-1 at fine index n j - 1
+  constexpr int B = 8;      // loads issued ahead of the elimination
+  T cp = T(0), dp = T(0);
+  for (int j0 = 1; j0 <= nv; j0 += B) {
+    T g[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int j = j0 + k;
+      g[k] = T(0);
+      if (j <= nv) g[k] = f[line + (long long)(NORD * j - 1) * P.inner] + scr[(long long)(j - 1) * npen + pen];
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int j = j0 + k;
+      if (j <= nv) {
+        const T inv = band_recip<T>(Dg - off * cp);
+        dp = (g[k] - off * dp) * inv;
+        cp = off * inv;
+        scr[(long long)(j - 1) * npen + pen] = cp;
+        f[line + (long long)(NORD * j - 1) * P.inner] = dp;
+      }
+    }
+  }
+  T vnext = T(0);
+  for (int j0 = nv; j0 >= 1; j0 -= B) {
+    T d[B], c[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int j = j0 - k;
+      d[k] = c[k] = T(0);
+      if (j >= 1) {
+        d[k] = f[line + (long long)(NORD * j - 1) * P.inner];
+        c[k] = scr[(long long)(j - 1) * npen + pen];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int j = j0 - k;
+      if (j >= 1) {
+        vnext = d[k] - c[k] * vnext;
+        f[line + (long long)(NORD * j - 1) * P.inner] = vnext;
+      }
+    }
+  }
+}
+
+template <typename T, int NORD>
+__global__ void __launch_bounds__(kBandThreads) band_back_kernel(BandParams P, int TW) {
+  constexpr int NI = NORD - 1, NI1 = NI > 0 ? NI : 1;
+  using D = ElemData<T>;
+  if (NI == 0) return;
+  long long o, w;
+  int e;
+  if (!band_elem(P, TW, o, e, w)) return;
+  T* f = reinterpret_cast<T*>(P.f);
+  const long long line = o * (long long)P.M * P.inner + w;
+  const T* tab = reinterpret_cast<const T*>(P.tab) + w * (NORD + 2);
+  const T beta = tab[0], alpha = T(P.alpha);
+  const T vl = e >= 1 ? f[line + (long long)(NORD * e - 1) * P.inner] : T(0);
+  const T vr = e <= P.K - 2 ? f[line + (long long)(NORD * e + NORD - 1) * P.inner] : T(0);
+  T t[NI1];
+#pragma unroll
+  for (int l = 0; l < NI; ++l) {
+    const T el = alpha * D::pta(P, l, 0) + beta * D::ptc(P, l, 0);
+    const T er = alpha * D::pta(P, l, 1) + beta * D::ptc(P, l, 1);
+    t[l] = fma(el, vl, er * vr) * tab[1 + l];
+  }
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const long long g = line + (long long)(NORD * e + i) * P.inner;
+    T acc = f[g];
+#pragma unroll
+    for (int l = 0; l < NI; ++l) acc = fma(-D::phi(P, i * NI + l), t[l], acc);
+    f[g] = acc;
+  }
+}
+
+template <typename T, int NORD>
+int launch_band_n(const BandParams& P, cudaStream_t s) {
+  int TW = 1;
+  while (TW * 2 <= 32 && TW * 2 <= P.inner) TW *= 2;
+  const int TE = kBandThreads / TW;
+  const long long blocks = P.outer * ((P.inner + TW - 1) / TW) * ((P.K + TE - 1) / TE);
+  const long long npen = P.outer * P.inner;
+  band_condense_kernel<T, NORD><<<(unsigned)blocks, kBandThreads, 0, s>>>(P, TW);
+  band_vertex_kernel<T, NORD><<<(unsigned)((npen + kBandThreads - 1) / kBandThreads), kBandThreads, 0, s>>>(P);
+  band_back_kernel<T, NORD><<<(unsigned)blocks, kBandThreads, 0, s>>>(P, TW);
+  return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_band_t(const BandParams& P, cudaStream_t s) {
+  switch (P.n) {
+    case 1: return launch_band_n<T, 1>(P, s);
+    case 2: return launch_band_n<T, 2>(P, s);
+    case 3: return launch_band_n<T, 3>(P, s);
+    case 4: return launch_band_n<T, 4>(P, s);
+    case 5: return launch_band_n<T, 5>(P, s);
+    case 6: return launch_band_n<T, 6>(P, s);
+    case 7: return launch_band_n<T, 7>(P, s);
+    case 8: return launch_band_n<T, 8>(P, s);
+    case 9: return launch_band_n<T, 9>(P, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+int launch_band(const BandParams& P, bool f64, cudaStream_t s) {
+  if (P.outer * P.inner <= 0 || P.K < 2) return 0;
+  return f64 ? launch_band_t<double>(P, s) : launch_band_t<float>(P, s);
+}
+
+}  // namespace femfft

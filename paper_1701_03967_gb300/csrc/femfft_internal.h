@@ -30,6 +30,12 @@ struct AxisHost {
 // Precompute the tables of one axis.  Returns 0 or a negative status.
 int precompute_axis(int n, int K, double X, double a, AxisHost* out);
 
+// Generalized eigenpairs of the interior blocks of the reference element
+// matrices, A_ii phi = nu C_ii phi (the bubble modes of Section 2), nu
+// ascending, columns of phi ((n-1) x (n-1), row-major) C_ii-orthonormal.
+// Returns 0 or a negative status; empty for n = 1.
+int interior_eig(int n, std::vector<double>* nu, std::vector<double>* phi);
+
 // Reference-element matrices rounded to double ((n+1)^2, row-major) and the
 // row sums of C (those of A are exactly zero).
 void reference_matrices(int n, std::vector<double>* A, std::vector<double>* C, std::vector<double>* Crow);

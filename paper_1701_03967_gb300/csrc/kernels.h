@@ -53,4 +53,27 @@ struct ApplyParams {
 
 int launch_apply(const ApplyParams& P, cudaStream_t s);
 
+// Algorithm (b) along axis 0 (band.cu): the 1D problems
+// [alpha calA + beta_w calC] v = y, one per position w of the later axes, on
+// a field viewed as [outer][M][inner], in place.
+constexpr int kBandMaxInt = kMaxOrder - 1;   // interior unknowns of an element
+struct BandParams {
+  void* f;             // the field (T = float or double), in place
+  const void* tab;     // T [inner][n + 2]: beta, r_0..r_{n-2} = 1 / (alpha nu_m + beta), D, off
+  void* scr;           // T [K - 1][outer * inner]: right-vertex contributions, then Thomas coefficients
+  long long outer, inner;
+  int M, K, n;
+  double alpha;        // a_1 4 h_1^-2
+  // element data: phi[i][l] (C_ii-orthonormal eigenvectors of A_ii phi = nu C_ii phi),
+  // pta / ptc [l][b] = (phi^T A_ib / phi^T C_ib) for b = left, right vertex,
+  // abi / cbi [b][m] = rows 0 and n of A / C over the interior columns
+  double phi[kBandMaxInt * kBandMaxInt];
+  double pta[kBandMaxInt][2], ptc[kBandMaxInt][2];
+  double abi[2][kBandMaxInt], cbi[2][kBandMaxInt];
+  float phif[kBandMaxInt * kBandMaxInt];
+  float ptaf[kBandMaxInt][2], ptcf[kBandMaxInt][2];
+  float abif[2][kBandMaxInt], cbif[2][kBandMaxInt];
+};
+int launch_band(const BandParams& P, bool f64, cudaStream_t s);
+
 }  // namespace femfft

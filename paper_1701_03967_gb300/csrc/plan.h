@@ -95,6 +95,14 @@ struct fem_fft_plan_s {
     int W = 0, V = 0;
   };
   Tuned tuned[3][femfft::kMaxN][2];
+  // algorithm (b) of Section 4 (fem_fft_set_algorithm): band-solve tables
+  // per position of the later axes (float64 and float32 copies), the element
+  // data and the vertex-solve scratch
+  int algo = 0;                        // 0: algorithm (a), 1: algorithm (b)
+  void* band_tab64 = nullptr;
+  void* band_tab32 = nullptr;
+  void* band_scr = nullptr;
+  femfft::BandParams band_proto;
   // kernel timing (fem_fft_profile)
   struct ProfRec {
     cudaEvent_t a, b;

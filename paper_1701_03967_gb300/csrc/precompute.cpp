@@ -285,6 +285,27 @@ static int sym_def_eig(int m, const std::vector<dd>& A, const std::vector<dd>& B
 
 // -------------------------------------------------------------- axis tables
 
+int interior_eig(int n, std::vector<double>* nu, std::vector<double>* phi) {
+  nu->clear();
+  phi->clear();
+  if (n < 2) return 0;
+  std::vector<dd> A, C;
+  reference_matrices_dd(n, &A, &C);
+  const int n1 = n + 1, m = n - 1;
+  std::vector<dd> At(m * m), Ct(m * m), lam, E;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      At[i * m + j] = A[(i + 1) * n1 + (j + 1)];
+      Ct[i * m + j] = C[(i + 1) * n1 + (j + 1)];
+    }
+  if (sym_def_eig(m, At, Ct, &lam, &E)) return -2;
+  nu->resize(m);
+  phi->resize(m * m);
+  for (int l = 0; l < m; ++l) (*nu)[l] = lam[l].to_double();
+  for (int i = 0; i < m * m; ++i) (*phi)[i] = E[i].to_double();
+  return 0;
+}
+
 int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
   if (n < 1 || n > kMaxOrder || K < 2) return -1;
   AxisHost& ax = *out;

@@ -223,6 +223,18 @@ def test_heat_step_decays_eigenmodes_exactly():
     np.testing.assert_allclose(got, factor * u, rtol=1e-11, atol=1e-13)
 
 
+@pytest.mark.parametrize("case", [c for c in CASES if len(c["K"]) > 1])
+def test_algorithm_b_matches_brute_force_dense_solve(case):
+    """Algorithm (b) (transforms in x_2..x_N, banded Cholesky in x_1) solves
+    the same assembled system as the dense solve."""
+    p = solve.Problem(case["n"], case["K"], case["X"], case["a"], case["c"])
+    b = synth.normal_batch(2, p.M, synth.CFG_TEST, 13)
+    L = solve.assemble_dense(p)
+    want = np.linalg.solve(L, b.reshape(2, -1).T).T.reshape(b.shape)
+    got = solve.solve_b(p, b)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
+
+
 def test_paper_error_tables():
     """Section 5 error tables (algorithm (a)) for K <= 32 (2D) and K <= 8 (3D):
     entries above the round-off floor agree to the two printed digits; below
