@@ -15,7 +15,9 @@
  *   and b is the "FEM average" right-hand side f^h.
  *   Solve (Section 4, algorithm (a)): direct FC_n-transform along every axis
  *   (Section 3, Theorem 2, item 2), division by sum_i a_i 4 h_i^-2 lambda_i + c,
- *   inverse F_n-transform along every axis (Theorem 2, item 1).
+ *   inverse F_n-transform along every axis (Theorem 2, item 1).  Algorithm (b)
+ *   of Section 4 (transforms along x_2..x_N, band solves along x_1) is
+ *   selected per plan by fem_fft_set_algorithm.
  *
  * Data layout (all entry points): a field is a C-order array
  *   [nrhs][M_1][M_2]...[M_N] of float64, M_i = n K_i - 1, axis N contiguous.

@@ -357,9 +357,8 @@ int run_band(fem_fft_plan p, long long nrhs, bool f64, void* work, cudaStream_t 
 
 // Tables of algorithm (b): for every position w of the later axes
 // beta_w = c + sum_{i>=1} a_i s_i lambda_i, r_m = 1 / (alpha nu_m + beta_w) and
-// the vertex system D = S_00 + S_11, off = S_01 of the element Schur
-// complement; element data from the interior eigenpairs of the reference
-// matrices.
+// the vertex system of the element Schur complement (sigma or D, and off);
+// element data from the interior eigenpairs of the reference matrices.
 int build_band_tables(fem_fft_plan p, cudaStream_t s) {
   const int n = p->n, n1 = n + 1, NI = n - 1;
   std::vector<double> nu, phi;
@@ -415,20 +414,37 @@ int build_band_tables(fem_fft_plan p, cudaStream_t s) {
     }
     double* t = &tab[(size_t)w * RB];
     t[0] = beta;
-    double S[2][2];
-    for (int x = 0; x < 2; ++x)
-      for (int y = 0; y < 2; ++y) S[x][y] = B.alpha * A[bi[x] * n1 + bi[y]] + beta * C[bi[x] * n1 + bi[y]];
+    // Vertex system of the element Schur complement S (bisymmetric):
+    // tridiag(off, D, off) = 2 delta I - off tridiag(-1, 2, -1), with
+    // off = S_01 and the row sum delta = S_00 + S_01.  Since A 1 = 0,
+    // S 1 = beta (Crow_b - E_bi E_ii^-1 Crow_i): delta carries no terms of
+    // size alpha, while D = S_00 + S_11 would be a difference of them (for the
+    // lowest modes D and 2 |off| agree to many digits).  Long double for both.
+    typedef long double ld;
+    const ld al = (ld)B.alpha, be = (ld)beta;
+    ld S01 = al * (ld)A[bi[0] * n1 + bi[1]] + be * (ld)C[bi[0] * n1 + bi[1]];
+    std::vector<ld> pcrow(NI, 0.0L);   // Phi^T Crow_i
     for (int m = 0; m < NI; ++m) {
-      const double r = 1.0 / (B.alpha * nu[m] + beta);
-      t[1 + m] = r;
-      const double e0 = B.alpha * pta[m * 2] + beta * ptc[m * 2];
-      const double e1 = B.alpha * pta[m * 2 + 1] + beta * ptc[m * 2 + 1];
-      S[0][0] -= e0 * r * e0;
-      S[0][1] -= e0 * r * e1;
-      S[1][1] -= e1 * r * e1;
+      ld acc = 0.0L;
+      for (int i = 0; i < NI; ++i) acc += (ld)phi[i * NI + m] * (ld)p->Crow[i + 1];
+      pcrow[m] = acc;
     }
-    t[n] = S[0][0] + S[1][1];
-    t[n + 1] = S[0][1];
+    ld rowc = (ld)p->Crow[0];          // Crow_0 - E_0i E_ii^-1 Crow_i
+    for (int m = 0; m < NI; ++m) {
+      const ld r = 1.0L / (al * (ld)nu[m] + be);
+      t[1 + m] = (double)r;
+      const ld e0 = al * (ld)pta[m * 2] + be * (ld)ptc[m * 2];
+      const ld e1 = al * (ld)pta[m * 2 + 1] + be * (ld)ptc[m * 2 + 1];
+      S01 -= e0 * r * e1;
+      rowc -= e0 * r * pcrow[m];
+    }
+    const ld delta = be * rowc;
+    if (S01 < 0.0L) {
+      t[n] = (double)(2.0L * delta / -S01);   // sigma: T = (-off) (sigma I + tridiag(-1, 2, -1))
+    } else {
+      t[n] = (double)(2.0L * delta - 2.0L * S01);   // D: strongly diagonally dominant here
+    }
+    t[n + 1] = (double)S01;
   }
   int rc;
   if (!p->band_tab64 && (rc = dev_alloc(p, &p->band_tab64, tab.size() * sizeof(double)))) return rc;

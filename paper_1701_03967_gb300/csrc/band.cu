@@ -12,10 +12,17 @@
 //     r_m = 1 / (alpha nu_m + beta); z = E_ii^-1 y_i replaces the interiors,
 //     the condensed right-hand side y_v - E_bi z is formed for the vertices;
 //  2. per 1D problem (parallel over w): the vertex system is symmetric
-//     tridiagonal with constant coefficients (D = S_00 + S_11, off = S_01 of
-//     the element Schur complement S = E_bb - E_bi E_ii^-1 E_ib) and is solved
-//     by Gaussian elimination without pivoting (Thomas algorithm; stable for
-//     symmetric positive definite matrices);
+//     tridiagonal with constant coefficients from the element Schur
+//     complement S = E_bb - E_bi E_ii^-1 E_ib: tridiag(off, D, off) =
+//     2 delta I - off T2, T2 = tridiag(-1, 2, -1), off = S_01, delta its row
+//     sum.  For off < 0 (stiffness-dominated) it is solved as
+//     (-off)(sigma I + T2) with sigma = 2 delta / (-off), by elimination
+//     whose pivots 1 + e_j, e_1 = 1 + sigma, e_j = sigma + e_{j-1} / (1 + e_{j-1})
+//     involve no cancellation (the plain form subtracts numbers that agree to
+//     many digits for the lowest modes, where the system is nearly the
+//     singular T2); for off >= 0 (mass-dominated, strongly diagonally
+//     dominant) by plain elimination.  No pivoting: the matrices are
+//     symmetric positive definite;
 //  3. per element (parallel): interiors v_i = z - E_ii^-1 E_ib v_b.
 // Every thread writes only its own element's slots; the right-vertex
 // contribution of element e goes to a scratch row and is added by the
@@ -123,10 +130,15 @@ __global__ void __launch_bounds__(kBandThreads) band_vertex_kernel(BandParams P)
   T* scr = reinterpret_cast<T*>(P.scr);
   const long long line = o * (long long)P.M * P.inner + w;
   const T* tab = reinterpret_cast<const T*>(P.tab) + w * (NORD + 2);
-  const T Dg = tab[NORD], off = tab[NORD + 1];
+  const T sd = tab[NORD], off = tab[NORD + 1];
+  const bool stiff = off < T(0);
+  // stiff: (sigma I + T2) v = g / (-off), eliminated with sub-diagonal -1;
+  // else: tridiag(off, D, off) v = g, eliminated with sub-diagonal off
+  const T scale = stiff ? band_recip<T>(-off) : T(1);
+  const T sub = stiff ? T(-1) : off;
   const int nv = P.K - 1;   // vertices j = 1..K-1 at fine index n j - 1
   constexpr int B = 8;      // loads issued ahead of the elimination
-  T cp = T(0), dp = T(0);
+  T e = T(0), cp = T(0), dp = T(0);
   for (int j0 = 1; j0 <= nv; j0 += B) {
     T g[B];
 #pragma unroll
@@ -139,14 +151,22 @@ __global__ void __launch_bounds__(kBandThreads) band_vertex_kernel(BandParams P)
     for (int k = 0; k < B; ++k) {
       const int j = j0 + k;
       if (j <= nv) {
-        const T inv = band_recip<T>(Dg - off * cp);
-        dp = (g[k] - off * dp) * inv;
-        cp = off * inv;
+        T inv;
+        if (stiff) {
+          e = (j == 1) ? T(1) + sd : sd + e * cp;   // pivot 1 + e_j; cp holds 1 / (1 + e_{j-1})
+          inv = band_recip<T>(T(1) + e);
+        } else {
+          inv = band_recip<T>(sd - off * cp);       // cp holds off / pivot_{j-1}
+        }
+        dp = (g[k] * scale - sub * dp) * inv;
+        cp = stiff ? inv : off * inv;
         scr[(long long)(j - 1) * npen + pen] = cp;
         f[line + (long long)(NORD * j - 1) * P.inner] = dp;
       }
     }
   }
+  // back substitution v_j = dp_j - c_j v_{j+1}, c_j = super / pivot_j
+  const T sup = stiff ? T(-1) : T(1);
   T vnext = T(0);
   for (int j0 = nv; j0 >= 1; j0 -= B) {
     T d[B], c[B];
@@ -163,7 +183,7 @@ __global__ void __launch_bounds__(kBandThreads) band_vertex_kernel(BandParams P)
     for (int k = 0; k < B; ++k) {
       const int j = j0 - k;
       if (j >= 1) {
-        vnext = d[k] - c[k] * vnext;
+        vnext = d[k] - sup * c[k] * vnext;
         f[line + (long long)(NORD * j - 1) * P.inner] = vnext;
       }
     }

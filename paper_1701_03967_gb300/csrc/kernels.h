@@ -59,7 +59,8 @@ int launch_apply(const ApplyParams& P, cudaStream_t s);
 constexpr int kBandMaxInt = kMaxOrder - 1;   // interior unknowns of an element
 struct BandParams {
   void* f;             // the field (T = float or double), in place
-  const void* tab;     // T [inner][n + 2]: beta, r_0..r_{n-2} = 1 / (alpha nu_m + beta), D, off
+  const void* tab;     // T [inner][n + 2]: beta, r_0..r_{n-2} = 1 / (alpha nu_m + beta), then
+                       // sigma (off < 0) or D (off >= 0), then off (the vertex system below)
   void* scr;           // T [K - 1][outer * inner]: right-vertex contributions, then Thomas coefficients
   long long outer, inner;
   int M, K, n;

@@ -6,10 +6,8 @@ launch configuration the benchmark times (default plans, max_nrhs = 1).
 2D: n = 9, K = 1024 x 1024 on [0,1]x[0,2], a = (1, 2.5), c = 1 (84.9 M DOF).
 3D: n = 9, K = 64^3 (190.1 M DOF) and n = 4, K = 128^3 (133.4 M DOF), unit cube,
     a = (1,1,1), c = 0.
-Both algorithms of Section 4.  Tolerances: relative L2 1e-12 (FP64 path,
-algorithm (a)), 1e-11 (FP64 path, algorithm (b): banded elimination, stable to
-about 1e-11 per Section 5) and 1e-10 (mixed path after its default
-refinement, either algorithm)."""
+Both algorithms of Section 4.  Tolerances: relative L2 1e-12 (FP64 path) and
+1e-10 (mixed path after its default refinement), for either algorithm."""
 
 import numpy as np
 import pytest
@@ -35,8 +33,8 @@ def test_fullsize_fp64_and_mixed_match_oracle(name, wl, cfg):
     want = osolve.solve(prob, b)
     nrm = np.linalg.norm(want)
     bt = torch.from_numpy(b).cuda()
-    # algorithm (a); algorithm (b) at its FP64 bar of 1e-11 (Section 5 reports it stable to about 1e-11)
-    for algo, precision, tol in (("a", "fp64", 1e-12), ("a", "mixed", 1e-10), ("b", "fp64", 1e-11),
+    # both algorithms of Section 4 at the same bars
+    for algo, precision, tol in (("a", "fp64", 1e-12), ("a", "mixed", 1e-10), ("b", "fp64", 1e-12),
                                  ("b", "mixed", 1e-10)):
         plan = Plan(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"], precision=precision)
         plan.set_algorithm(algo)
