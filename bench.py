@@ -195,7 +195,8 @@ def run_batched(torch, args, barrier):
     """The batched workload (256 seeded problems, N in {2,3}, n in 2..8, K_i in
     {16,...,512}, 1-8 right-hand sides): one graph launch of the batched
     mixed solver against the same problems solved one after another with
-    stand-alone FP64 plans.  Right-hand sides N(0,1) drawn on the device."""
+    stand-alone FP64 plans, with every plan on algorithm (a), then on
+    algorithm (b).  Right-hand sides N(0,1) drawn on the device."""
     from paper_1701_03967_gb300 import Batch, Plan, synth
     specs = synth.batched_problems()
     plans = [Plan(s["n"], s["K"], s["X"], s["a"], s["c"], "mixed", max_nrhs=s["nrhs"]) for s in specs]
@@ -222,6 +223,18 @@ def run_batched(torch, args, barrier):
            "value": units / (ms_b * 1e-3), "unit": "DOF/s", "ms_per_solve": ms_b,
            "fp64_sequential": {"value": units / (ms_64 * 1e-3), "ms_per_solve": ms_64},
            "rel_vs_fp64": rel, "create_s": t_create, "launches_per_solve": len({s["n"] for s in specs})}
+    batch.close()
+    # the same problems with every plan on algorithm (b), batched and sequential FP64
+    for pl in plans + p64:
+        pl.set_algorithm("b")
+    batch = Batch(plans, [s["nrhs"] for s in specs])
+    ms_bb = time_steps(torch, lambda: batch.solve(b, out=u), max(2, args.steps // 2), args.warmup, barrier)
+    batch.check()
+    rel_b = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
+    ms_64b = time_steps(torch, seq64, max(2, args.steps // 2), args.warmup, barrier)
+    out["algo_b"] = {"value": units / (ms_bb * 1e-3), "ms_per_solve": ms_bb, "steps": batch.n_steps,
+                     "items": batch.n_items, "rel_vs_fp64_a": rel_b,
+                     "fp64_sequential": {"value": units / (ms_64b * 1e-3), "ms_per_solve": ms_64b}}
     batch.close()
     for pl in p64 + plans:
         pl.close()

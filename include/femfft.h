@@ -148,8 +148,9 @@ int fem_fft_apply_mass(fem_fft_plan plan, const double* d_u, double* d_b, int64_
  * interiors and a tridiagonal vertex solve.  Both give the solution of
  * L u = b.  Setting B computes its tables (one row of n + 2 values per
  * position of x_2..x_N) and a scratch of max_nrhs * (K_1 - 1) * M_2..M_N
- * values; synchronises stream.  FEM_FFT_ERR_ARG for N = 1 or with batches
- * (a plan set to B cannot join fem_fft_batch_create).
+ * values; synchronises stream.  FEM_FFT_ERR_ARG for N = 1.  A batch
+ * (fem_fft_batch_create) runs each plan's algorithm as set when the batch is
+ * created.
  */
 enum { FEM_FFT_ALGO_A = 0, FEM_FFT_ALGO_B = 1 };
 int fem_fft_set_algorithm(fem_fft_plan plan, int algo, void* stream);
@@ -268,8 +269,8 @@ int fem_fft_apply_noalloc(int N, int n, const int64_t* h_K, const double* h_X, c
  * dependency-driven kernel launch that runs every step of every problem of
  * that order from a ticket-ordered work list).  Each problem
  * is solved as fem_fft_solve would solve it with a mixed-precision plan:
- * algorithm (a) of Section 4 in float32, then `steps` float64 residual
- * refinement steps.  The batch is an execution schedule over existing plans;
+ * the plan's algorithm of Section 4 ((a), or (b) with its band solve as three
+ * batch steps) in float32, then `steps` float64 residual refinement steps.  The batch is an execution schedule over existing plans;
  * it owns no copy of their tables or workspaces.
  *
  * fem_fft_batch_create -- record the solve chains of nprob plans and build

@@ -89,7 +89,7 @@ class Plan:
 
     # -- solver ----------------------------------------------------------
     def solve(self, b, out=None, stream=None):
-        """u = L^{-1} b (Section 4, algorithm (a))."""
+        """u = L^{-1} b (Section 4: algorithm (a), or (b) after set_algorithm("b"))."""
         nrhs = self._field(b, "b")
         u = self._out(b, out)
         _lib.check(_lib.lib().fem_fft_solve(self._h, b.data_ptr(), u.data_ptr(), nrhs, self._stream(stream)),

@@ -334,15 +334,20 @@ int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const
 
 // Algorithm (b) along axis 0, in place on the work array (N >= 2).
 int run_band(fem_fft_plan p, long long nrhs, bool f64, void* work, cudaStream_t s) {
-  if (p->rec) {
-    set_last_error("algorithm (b) has no batched form");
-    return FEM_FFT_ERR_ARG;
-  }
   BandParams B = p->band_proto;
   B.f = work;
   B.tab = f64 ? p->band_tab64 : p->band_tab32;
   B.scr = p->band_scr;
   B.outer = nrhs;
+  if (p->rec) {
+    RecordedOp op;
+    std::memset(&op, 0, sizeof(op));
+    op.kind = 2;
+    op.mode = f64 ? 1 : 0;
+    op.bp = B;
+    p->rec->push_back(op);
+    return FEM_FFT_OK;
+  }
   const double elems = (double)nrhs * p->dof;
   // bytes of the three phases: field read + written twice, vertex rows twice
   const double bytes = elems * (f64 ? 8.0 : 4.0) * (4.0 + 4.0 / p->n);

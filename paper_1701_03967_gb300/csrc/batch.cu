@@ -636,6 +636,29 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
           free_batch(b);
           return batch_fail(FEM_FFT_ERR_ARG, "batch: a pencil does not fit the batch kernel's shared memory");
         }
+      } else if (op.kind == 2) {
+        // algorithm (b): condensation, vertex solve, back substitution
+        if (op.mode != 0) {
+          free_batch(b);
+          return batch_fail(FEM_FFT_ERR_ARG, "batch: band solves run in float32 only");
+        }
+        const BandParams& B = op.bp;
+        const int TW = band_tw(B.inner);
+        const long long eblocks = band_elem_blocks(B, TW);
+        for (int phase = 0; phase < 3; ++phase) {
+          BatchStage bs;
+          std::memset(&bs, 0, sizeof(bs));
+          bs.kind = BATCH_BAND;
+          bs.mode = phase;
+          bs.n = B.n;
+          bs.TW = TW;
+          bs.bp = B;
+          bs.units = phase == 1 ? band_vertex_blocks(B) : eblocks;
+          bs.units_per_item =
+              phase == 1 ? 1 : (int)std::max<long long>(1, kItemDof / ((long long)kBandThreads * B.n));
+          if (phase == 2 && B.n == 1) continue;   // no interiors to recover
+          psteps[p].push_back(bs);
+        }
       } else {
         if (op.ap.nout > 2 || op.ap.dotv || op.ap.norms) {
           free_batch(b);
@@ -683,6 +706,7 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
     for (size_t i = 0; i < total; ++i) {
       const BatchStage& st = psteps[probs[oprob[i]]][ostep[i]];
       if (st.kind == BATCH_PENCIL) g.smem = std::max(g.smem, pencil_smem(st.pp));
+      else if (st.kind == BATCH_BAND) g.smem = std::max(g.smem, sizeof(BandParams));
       else g.smem = std::max(g.smem, batch_apply_smem<kMaxOrder>() + (size_t)st.tile_smem);
       g.stages.push_back(st);
       prev[i] = last[oprob[i]];

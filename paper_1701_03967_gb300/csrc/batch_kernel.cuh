@@ -1,9 +1,10 @@
 // The dependency-driven kernel of the batched solver (one instantiation per
 // element order n) and the work-list records it reads.
 //
-// Work list.  Every problem's mixed-precision solve (algorithm (a) of
+// Work list.  Every problem's mixed-precision solve (algorithm (a) or (b) of
 // Section 4 in float32, then float64 residual refinement) is a linear chain
-// of steps: pencil passes along the axes and operator applies.  A step is cut
+// of steps: pencil passes along the axes, the three phases of the band solve
+// of algorithm (b) and operator applies.  A step is cut
 // into items (one pass tile, or a few apply blocks); every item of step s of
 // a problem needs all items of step s-1 of the same problem.  The items are
 // numbered in "level" order (step 0 of every problem, then step 1 of every
@@ -28,6 +29,7 @@
 
 #include "../../include/femfft.h"
 #include "apply.cuh"
+#include "band.cuh"
 #include "pencil.cuh"
 
 namespace femfft {
@@ -36,14 +38,15 @@ constexpr int kBatchThreads = 256;
 constexpr int kBatchCtasPerSm = 4;   // resident CTAs overlap one another's prologue and barriers (measured: 4 > 3 > 2)
 constexpr long long kItemDof = 1 << 16;  // target unknowns per item
 constexpr unsigned kMaxSpin = 1u << 24;  // hard iteration bound of a dependency wait
+static_assert(kBandThreads == kBatchThreads, "band blocks are laid out for the batch kernel's block size");
 
-enum BatchKind { BATCH_PENCIL = 0, BATCH_APPLY = 1 };
+enum BatchKind { BATCH_PENCIL = 0, BATCH_APPLY = 1, BATCH_BAND = 2 };
 
 struct BatchStage {
   int kind;           // BatchKind
-  int mode;           // pencil: MODE_*; apply: number of outputs (1 or 2)
+  int mode;           // pencil: MODE_*; apply: number of outputs (1 or 2); band: phase (0 condense, 1 vertex, 2 back)
   int n;
-  int TW;             // apply: positions of the contiguous axis per block
+  int TW;             // apply, band: positions of the contiguous axis per block
   int dep;            // index of the step this one waits for (-1: none)
   unsigned need;      // items of that step
   int units_per_item;
@@ -53,6 +56,7 @@ struct BatchStage {
   long long items;
   PassParams pp;
   ApplyParams ap;
+  BandParams bp;      // float32 field and tables
 };
 
 struct BatchArgs {
@@ -173,6 +177,18 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchCtasPerSm) batch_kernel(B
     else if (mode == MODE_INV) pencil_tile<float, NORD, MODE_INV, kMaxW, false>(s_pp, u0, smem, s_base, true);
     else if (mode == MODE_FWD_DIV) pencil_tile<float, NORD, MODE_FWD_DIV, kMaxW, false>(s_pp, u0, smem, s_base, true);
     else pencil_tile<float, NORD, MODE_FUSED, kMaxW, false>(s_pp, u0, smem, s_base, true);
+  } else if (kind == BATCH_BAND) {
+    BandParams* bp = reinterpret_cast<BandParams*>(smem);
+    const int* src = reinterpret_cast<const int*>(&S.bp);
+    int* dst = reinterpret_cast<int*>(bp);
+    for (int i = threadIdx.x; i < (int)(sizeof(BandParams) / sizeof(int)); i += blockDim.x) dst[i] = __ldg(&src[i]);
+    __syncthreads();
+    // blocks are independent: no barrier between them
+    for (long long b = u0; b < u1; ++b) {
+      if (mode == 0) band_condense_block<float, NORD, true>(*bp, S.TW, b);
+      else if (mode == 1) band_vertex_block<float, NORD, true>(*bp, b);
+      else band_back_block<float, NORD, true>(*bp, S.TW, b);
+    }
   } else {
     ApplyParams* ap = reinterpret_cast<ApplyParams*>(smem + batch_apply_scratch<NORD>());
     const int* src = reinterpret_cast<const int*>(&S.ap);

@@ -26,10 +26,11 @@ struct DevTables {
 // kernel.  kind 0: pencil pass (pp, with the plan's own tile choice);
 // kind 1: operator apply (ap).
 struct RecordedOp {
-  int kind;
+  int kind;   // 0 pencil pass, 1 operator apply, 2 band solve (algorithm (b))
   int mode, axis;
   PassParams pp;
   ApplyParams ap;
+  BandParams bp;
 };
 
 void set_last_error(const std::string& what);

@@ -5,7 +5,7 @@ Tolerance: relative L2 1e-10 per problem (the mixed path after its default
 two refinement steps).  Also: repeated launches give identical bits, a change
 of buffers rewrites the step tables, the bounded dependency waits report
 FEM_FFT_ERR_TIMEOUT when a step can never start, and the autotune cache
-round-trips."""
+round-trips.  Plans on algorithm (b) of Section 4 batch as well."""
 
 import json
 import os
@@ -104,6 +104,28 @@ def test_bounded_wait_reports_timeout_then_recovers(small_batch):
     assert torch.equal(u, ref)
 
 
+def test_batch_with_algorithm_b_plans():
+    """Plans set to algorithm (b) (every N >= 2 problem but one) share a batch
+    with algorithm (a) plans: the three phases of the band solve run as batch
+    steps.  Every problem against the oracle at the mixed path's bar."""
+    from paper_1701_03967_gb300 import Batch
+    plans = _plans(SMALL)
+    algos = []
+    for i, (c, pl) in enumerate(zip(SMALL, plans)):
+        algo = "b" if len(c["K"]) >= 2 and i != 1 else "a"
+        if algo == "b":
+            pl.set_algorithm("b")
+        algos.append(algo)
+    assert algos.count("b") >= 6
+    batch = Batch(plans, [c["nrhs"] for c in SMALL])
+    rhs = _rhs(SMALL, synth.CFG_TEST)
+    u = batch.solve(batch.pack(rhs), check=True)
+    for c, algo, bp, up in zip(SMALL, algos, rhs, batch.views(u)):
+        prob = osolve.Problem(c["n"], c["K"], c.get("X"), c.get("a"), c.get("c", 0.0))
+        rel = _rel(up.cpu().numpy(), osolve.solve(prob, bp))
+        assert rel <= 1e-10, (c, algo, rel)
+
+
 def test_tuning_cache_round_trip(tmp_path):
     from paper_1701_03967_gb300 import Batch
     cases = SMALL[:4]
@@ -142,14 +164,18 @@ def test_batch_rejects_fp64_and_repeated_plans():
         Batch(pm, [SMALL[0]["nrhs"] + 1])      # more right-hand sides than max_nrhs
 
 
-def test_batched_workload_256_problems():
+@pytest.mark.parametrize("algo", ["a", "b"])
+def test_batched_workload_256_problems(algo):
     """The batched workload: 256 seeded problems (N in {2,3}, n in 2..8, K_i in
-    {16,32,48,96,128,384,512}, 1-8 right-hand sides).  Every problem against
-    the stand-alone FP64 plan (itself held to 1e-12 of the oracle by the other
-    parity tests) and the four smallest against the oracle directly."""
+    {16,32,48,96,128,384,512}, 1-8 right-hand sides), every plan on algorithm
+    (a) or every plan on algorithm (b).  Every problem against the stand-alone
+    FP64 plan (itself held to 1e-12 of the oracle by the other parity tests)
+    and the four smallest against the oracle directly."""
     from paper_1701_03967_gb300 import Batch, Plan
     specs = synth.batched_problems()
     plans = _plans(specs)
+    for pl in plans:
+        pl.set_algorithm(algo)
     batch = Batch(plans, [s["nrhs"] for s in specs])
     b = torch.empty(batch.total_len, dtype=torch.float64, device="cuda")
     for pid, (s, v) in enumerate(zip(specs, batch.views(b))):
@@ -171,5 +197,5 @@ def test_batched_workload_256_problems():
         prob = osolve.Problem(s["n"], s["K"], s["X"], s["a"], s["c"])
         want = osolve.solve(prob, batch.views(b)[pid].cpu().numpy())
         assert _rel(batch.views(u)[pid].cpu().numpy(), want) <= 1e-10
-    print(f"256 problems, {batch.total_len} DOF x rhs, {batch.n_steps} steps, {batch.n_items} items; "
+    print(f"algorithm ({algo}): 256 problems, {batch.total_len} DOF x rhs, {batch.n_steps} steps, {batch.n_items} items; "
           f"worst rel vs FP64 plan {worst:.3e}")

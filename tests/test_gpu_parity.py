@@ -266,11 +266,7 @@ def test_algorithm_b_matches_oracle(case, precision, tol):
     assert _rel(got2, osolve.solve(prob2, b)) <= tol
 
 
-def test_algorithm_b_is_rejected_by_batches():
-    from paper_1701_03967_gb300 import Batch, FemFftError
-    plan = _plan(dict(n=2, K=(8, 8)), "mixed")
-    plan.set_algorithm("b")
-    with pytest.raises(FemFftError):
-        Batch([plan], [1], tune=False)
+def test_algorithm_b_needs_two_axes():
+    from paper_1701_03967_gb300 import FemFftError
     with pytest.raises(FemFftError):
         _plan(dict(n=2, K=(8,)), "fp64").set_algorithm("b")
