@@ -321,45 +321,6 @@ __device__ __forceinline__ df ld_df(const double* x, bool is_df, long long plane
   return split_f64(ld_f64<NC>(x + off));
 }
 
-template <int NORD, bool NC>
-__device__ __forceinline__ void load_elem_df(const double* x, bool is_df, long long plane, long long line,
-                                             long long inner, int e, int M, df (&u)[NORD + 1]) {
-#pragma unroll
-  for (int q = 0; q <= NORD; ++q) {
-    const int g = NORD * e + q - 1;
-    u[q] = (g >= 0 && g < M) ? ld_df<NC>(x, is_df, plane, line + (long long)g * inner) : df{0.0f, 0.0f};
-  }
-}
-
-template <int NORD, bool ROW0_ONLY>
-__device__ __forceinline__ void elem_product_df(const df* Es, const df* Ea, const df* E1, bool has_e1,
-                                                const df (&u)[NORD + 1], df (&y)[NORD + 1]) {
-  using C = EO<NORD>;
-  const df ub = df_scale2(df_add(u[0], u[NORD]), 0.5f);
-  const df ub2 = df_scale2(ub, 2.0f);
-  df sv[C::P + 1], av[C::P];
-#pragma unroll
-  for (int j = 0; j < C::P; ++j) {
-    sv[j] = df_sub(df_add(u[j], u[NORD - j]), ub2);
-    av[j] = df_sub(u[j], u[NORD - j]);
-  }
-  sv[C::P] = (NORD % 2 == 0) ? df_sub(u[NORD / 2], ub) : df{0.0f, 0.0f};
-  constexpr int NS = (NORD % 2 == 0) ? C::SP : C::P;
-#pragma unroll
-  for (int q = 0; q < C::R; ++q) {
-    if (ROW0_ONLY && q > 0) break;
-    const df ts = df_dot<NS>(Es + q * C::SP, sv);
-    const df ta = df_dot<C::P>(Ea + q * C::P, av);
-    if (has_e1) {
-      y[q] = df_fma(ub, E1[q], df_add(ts, ta));
-      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = df_fma(ub, E1[NORD - q], df_sub(ts, ta));
-    } else {
-      y[q] = df_add(ts, ta);
-      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = df_sub(ts, ta);
-    }
-  }
-}
-
 // Input tiles of a double-float apply block, staged in shared memory before
 // any arithmetic so that all of the block's loads are in flight together
 // (the per-element loads of the unstaged form left the kernel waiting on
@@ -412,11 +373,57 @@ __device__ __forceinline__ df slot_df(uint2 v, bool is_df) {
   return split_f64(__longlong_as_double((long long)(((unsigned long long)v.y << 32) | v.x)));
 }
 
-template <int NORD>
-__device__ __forceinline__ void tile_elem_df(const uint2* tile, bool is_df, int TW, int te, int tw,
-                                             df (&u)[NORD + 1]) {
+// y = E u for one element (all n+1 rows, or only row 0 when ROW0_ONLY) in
+// the even/odd form of elem_product, reading u from a staged tile: u_q at
+// col[q * TW].  The columns are streamed (runtime loop over the pairs j,
+// n - j) and every row's compensated sum advances once per column, so the
+// loop body stays small (the fully unrolled row-by-row form overflowed the
+// instruction cache at n = 9) and the rows are independent chains.  Each
+// row sees its terms in the order j = 0, 1, ... as before; column 0 of Es'
+// multiplies s_0 = (u_0 + u_n) - 2 ub = 0 exactly and is skipped.
+template <int NORD, bool ROW0_ONLY>
+__device__ __forceinline__ void elem_product_df(const df* Es, const df* Ea, const df* E1, bool has_e1,
+                                                const uint2* col, int TW, bool is_df, df (&y)[NORD + 1]) {
+  using C = EO<NORD>;
+  constexpr int RR = ROW0_ONLY ? 1 : C::R;
+  const df u0 = slot_df(col[0], is_df), un = slot_df(col[NORD * TW], is_df);
+  const df ub = df_scale2(df_add(u0, un), 0.5f);
+  const df ub2 = df_scale2(ub, 2.0f);
+  float ss[RR], cs[RR], sa[RR], ca[RR];
 #pragma unroll
-  for (int q = 0; q <= NORD; ++q) u[q] = slot_df(tile[(NORD * te + q) * TW + tw], is_df);
+  for (int q = 0; q < RR; ++q) ss[q] = cs[q] = sa[q] = ca[q] = 0.0f;
+  {
+    const df av = df_sub(u0, un);
+#pragma unroll
+    for (int q = 0; q < RR; ++q) dot2_step(Ea[q * C::P], av, sa[q], ca[q]);
+  }
+#pragma unroll 1
+  for (int j = 1; j < C::P; ++j) {
+    const df uj = slot_df(col[j * TW], is_df), unj = slot_df(col[(NORD - j) * TW], is_df);
+    const df sv = df_sub(df_add(uj, unj), ub2);
+    const df av = df_sub(uj, unj);
+#pragma unroll
+    for (int q = 0; q < RR; ++q) {
+      dot2_step(Es[q * C::SP + j], sv, ss[q], cs[q]);
+      dot2_step(Ea[q * C::P + j], av, sa[q], ca[q]);
+    }
+  }
+  if (NORD % 2 == 0) {   // the middle node (even n)
+    const df sv = df_sub(slot_df(col[(NORD / 2) * TW], is_df), ub);
+#pragma unroll
+    for (int q = 0; q < RR; ++q) dot2_step(Es[q * C::SP + C::P], sv, ss[q], cs[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < RR; ++q) {
+    const df ts = {ss[q], cs[q]}, ta = {sa[q], ca[q]};
+    if (has_e1) {
+      y[q] = df_fma(ub, E1[q], df_add(ts, ta));
+      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = df_fma(ub, E1[NORD - q], df_sub(ts, ta));
+    } else {
+      y[q] = df_add(ts, ta);
+      if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = df_sub(ts, ta);
+    }
+  }
 }
 
 // Block bx of a double-float apply launch (same tiling as apply_block);
@@ -466,10 +473,10 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
     for (int q = 0; q < N1; ++q) acc[j][q] = df{0.0f, 0.0f};
   if (valid) {
     for (int t = 0; t < P.nterm; ++t) {
-      df u[N1], y[N1];
+      df y[N1];
       const int src = P.t_src[t];
-      tile_elem_df<NORD>(tin[src], P.in_df[src] != 0, TW, te, tw, u);
-      elem_product_df<NORD, false>(S.es[t], S.ea[t], S.e1[t], S.has1[t], u, y);
+      elem_product_df<NORD, false>(S.es[t], S.ea[t], S.e1[t], S.has1[t], tin[src] + NORD * te * TW + tw, TW,
+                                   P.in_df[src] != 0, y);
       const int d = P.t_dst[t];
 #pragma unroll
       for (int j = 0; j < NOUT; ++j)
@@ -491,10 +498,10 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
         for (int j = 0; j < NOUT; ++j) acc[j][NORD] = df_add(acc[j][NORD], S.row0[j][threadIdx.x + TW]);
       } else {
         for (int t = 0; t < P.nterm; ++t) {
-          df u[N1], y[N1];
+          df y[N1];
           const int src = P.t_src[t];
-          tile_elem_df<NORD>(tin[src], P.in_df[src] != 0, TW, te + 1, tw, u);
-          elem_product_df<NORD, true>(S.es[t], S.ea[t], S.e1[t], S.has1[t], u, y);
+          elem_product_df<NORD, true>(S.es[t], S.ea[t], S.e1[t], S.has1[t], tin[src] + NORD * (te + 1) * TW + tw,
+                                      TW, P.in_df[src] != 0, y);
           const int d = P.t_dst[t];
 #pragma unroll
           for (int j = 0; j < NOUT; ++j)

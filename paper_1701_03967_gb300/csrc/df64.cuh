@@ -63,28 +63,23 @@ __device__ __forceinline__ df df_fma(df a, df b, df acc) {
   return quick_two_sum(s.hi, s.lo);
 }
 
-// Compensated dot product of double-float vectors (Dot2 of T. Ogita,
-// S. M. Rump, S. Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
-// 26, 2005, with double-float operands): the hi parts of the products are
-// summed with two_sum, every rounding error and the cross terms go into one
-// float correction.  The carried dependency is one float addition per term
-// (df_fma renormalises after every term).  Result unnormalised (s, c).
-template <int L>
-__device__ __forceinline__ df df_dot(const df* a, const df* b) {
-  float s = 0.0f, c = 0.0f;
-#pragma unroll
-  for (int j = 0; j < L; ++j) {
-    const float p = a[j].hi * b[j].hi;
-    float e = fmaf(a[j].hi, b[j].hi, -p);
-    e = fmaf(a[j].hi, b[j].lo, e);
-    e = fmaf(a[j].lo, b[j].hi, e);
-    const float t = s + p;
-    const float z = t - s;
-    const float sig = (s - (t - z)) + (p - z);
-    s = t;
-    c += sig + e;
-  }
-  return {s, c};
+// One term of a compensated dot product of double-float vectors (Dot2 of
+// T. Ogita, S. M. Rump, S. Oishi, "Accurate sum and dot product", SIAM J.
+// Sci. Comput. 26, 2005, with double-float operands): (s, c) += a * b.  The
+// hi parts of the products are summed into s with two_sum; every rounding
+// error and the cross terms go into the float correction c.  The carried
+// dependency is one float addition per term; the running value is the
+// unnormalised pair (s, c).
+__device__ __forceinline__ void dot2_step(df a, df b, float& s, float& c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float t = s + p;
+  const float z = t - s;
+  const float sig = (s - (t - z)) + (p - z);
+  s = t;
+  c += sig + e;
 }
 
 __device__ __forceinline__ df split_f64(double x) {
