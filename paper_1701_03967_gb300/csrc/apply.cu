@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_kernel(ApplyParams P, 
 template <int NORD, int NOUT>
 __global__ void __launch_bounds__(kApplyThreads, 4) apply_kernel_df(ApplyParams P, int TW) {
   __shared__ ApplySmemDF<NORD, NOUT, kApplyThreads> S;
-  extern __shared__ uint2 tiles[];
+  extern __shared__ float2 tiles[];
   apply_stage_mats_df<NORD, NOUT, kApplyThreads>(P, S);
   apply_block_df<NORD, NOUT, kApplyThreads, true>(P, TW, blockIdx.x, S, tiles);
 }
@@ -44,7 +44,7 @@ int launch_apply(const ApplyParams& P, cudaStream_t s) {
   const int TE = kApplyThreads / TW;
   const long long blocks = P.outer * ((P.inner + TW - 1) / TW) * ((P.K + TE - 1) / TE);
   if (P.df) {
-    if (P.dotv || P.nout > 2) return (int)cudaErrorInvalidValue;
+    if (!apply_df_form_ok(P)) return (int)cudaErrorInvalidValue;
     int nin = 0;
     for (int i = 0; i < kApplyMaxIn; ++i) nin += P.in[i] != nullptr;
     const size_t smem = apply_df_tile_bytes(P.n, TW, kApplyThreads, nin);

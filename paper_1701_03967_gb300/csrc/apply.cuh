@@ -327,8 +327,9 @@ __device__ __forceinline__ df ld_df(const double* x, bool is_df, long long plane
 // memory latency).  Rows: fine indices g0 = n e0 - 1 .. n (e0 + TE + 1) - 1,
 // i.e. the block's TE elements and the next element (whose row 0 the last
 // element row recomputes); columns: the block's TW positions of the
-// contiguous axis.  A slot holds 8 bytes: a float64 value or a (hi, lo)
-// float pair.
+// contiguous axis.  A slot holds the value as a (hi, lo) float pair: float64
+// inputs are split once here, so the element products read every input the
+// same way.
 __host__ __device__ constexpr int apply_df_rows(int n, int TE) { return n * (TE + 1) + 1; }
 inline size_t apply_df_tile_bytes(int n, int TW, int nthreads, int ninputs) {
   return (size_t)ninputs * apply_df_rows(n, nthreads / TW) * TW * 8;
@@ -338,7 +339,7 @@ constexpr int kStageBatch = 8;   // loads in flight per thread while staging
 
 template <bool NC>
 __device__ void stage_input_df(const double* x, bool is_df, long long plane, long long line0, long long inner,
-                               int g0, int rows, int TW, int wvalid, int M, uint2* tile) {
+                               int g0, int rows, int TW, int wvalid, int M, float2* tile) {
   const int total = rows * TW;
   const int tw_shift = __ffs(TW) - 1;   // TW is a power of two
   for (int i0 = threadIdx.x; i0 < total; i0 += kStageBatch * blockDim.x) {
@@ -363,15 +364,17 @@ __device__ void stage_input_df(const double* x, bool is_df, long long plane, lon
 #pragma unroll
     for (int k = 0; k < kStageBatch; ++k) {
       const int i = i0 + k * blockDim.x;
-      if (i < total) tile[i] = v[k];
+      if (i < total) {
+        df d;
+        if (is_df) d = {__uint_as_float(v[k].x), __uint_as_float(v[k].y)};
+        else d = split_f64(__longlong_as_double((long long)(((unsigned long long)v[k].y << 32) | v[k].x)));
+        tile[i] = make_float2(d.hi, d.lo);
+      }
     }
   }
 }
 
-__device__ __forceinline__ df slot_df(uint2 v, bool is_df) {
-  if (is_df) return {__uint_as_float(v.x), __uint_as_float(v.y)};
-  return split_f64(__longlong_as_double((long long)(((unsigned long long)v.y << 32) | v.x)));
-}
+__device__ __forceinline__ df slot_df(float2 v) { return {v.x, v.y}; }
 
 // y = E u for one element (all n+1 rows, or only row 0 when ROW0_ONLY) in
 // the even/odd form of elem_product, reading u from a staged tile: u_q at
@@ -379,14 +382,18 @@ __device__ __forceinline__ df slot_df(uint2 v, bool is_df) {
 // n - j) and every row's compensated sum advances once per column, so the
 // loop body stays small (the fully unrolled row-by-row form overflowed the
 // instruction cache at n = 9) and the rows are independent chains.  Each
-// row sees its terms in the order j = 0, 1, ... as before; column 0 of Es'
-// multiplies s_0 = (u_0 + u_n) - 2 ub = 0 exactly and is skipped.
+// row sees its terms in the order j = 0, 1, ...; column 0 of Es' multiplies
+// s_0 = (u_0 + u_n) - 2 ub = 0 exactly and is skipped.  Every sum is
+// renormalised: left unnormalised (lo parts of a few ulp of the operands, or
+// of a row's partial sums) they are multiplied in float by the next product,
+// which measured a floor of 1e-10 instead of ~1e-12 on the refined 2D n = 9
+// solve.
 template <int NORD, bool ROW0_ONLY>
 __device__ __forceinline__ void elem_product_df(const df* Es, const df* Ea, const df* E1, bool has_e1,
-                                                const uint2* col, int TW, bool is_df, df (&y)[NORD + 1]) {
+                                                const float2* col, int TW, df (&y)[NORD + 1]) {
   using C = EO<NORD>;
   constexpr int RR = ROW0_ONLY ? 1 : C::R;
-  const df u0 = slot_df(col[0], is_df), un = slot_df(col[NORD * TW], is_df);
+  const df u0 = slot_df(col[0]), un = slot_df(col[NORD * TW]);
   const df ub = df_scale2(df_add(u0, un), 0.5f);
   const df ub2 = df_scale2(ub, 2.0f);
   float ss[RR], cs[RR], sa[RR], ca[RR];
@@ -399,7 +406,7 @@ __device__ __forceinline__ void elem_product_df(const df* Es, const df* Ea, cons
   }
 #pragma unroll 1
   for (int j = 1; j < C::P; ++j) {
-    const df uj = slot_df(col[j * TW], is_df), unj = slot_df(col[(NORD - j) * TW], is_df);
+    const df uj = slot_df(col[j * TW]), unj = slot_df(col[(NORD - j) * TW]);
     const df sv = df_sub(df_add(uj, unj), ub2);
     const df av = df_sub(uj, unj);
 #pragma unroll
@@ -409,7 +416,7 @@ __device__ __forceinline__ void elem_product_df(const df* Es, const df* Ea, cons
     }
   }
   if (NORD % 2 == 0) {   // the middle node (even n)
-    const df sv = df_sub(slot_df(col[(NORD / 2) * TW], is_df), ub);
+    const df sv = df_sub(slot_df(col[(NORD / 2) * TW]), ub);
 #pragma unroll
     for (int q = 0; q < RR; ++q) dot2_step(Es[q * C::SP + C::P], sv, ss[q], cs[q]);
   }
@@ -430,7 +437,7 @@ __device__ __forceinline__ void elem_product_df(const df* Es, const df* Ea, cons
 // tiles: shared memory for the staged inputs (apply_df_tile_bytes).
 template <int NORD, int NOUT, int NTHREADS, bool NC>
 __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, long long bx,
-                                               ApplySmemDF<NORD, NOUT, NTHREADS>& S, uint2* tiles) {
+                                               ApplySmemDF<NORD, NOUT, NTHREADS>& S, float2* tiles) {
   using C = EO<NORD>;
   constexpr int N1 = C::N1;
   const int K = P.K;
@@ -452,7 +459,7 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
   const int g0 = NORD * (int)(et * TE) - 1;
   const int wvalid = (int)min((long long)TW, P.inner - w0);
   // stage every input the block uses
-  uint2* tin[kApplyMaxIn];
+  float2* tin[kApplyMaxIn];
   {
     int k = 0;
     for (int i = 0; i < kApplyMaxIn; ++i) {
@@ -466,23 +473,17 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
   }
   __syncthreads();
 
+  // term t writes output t (nterm == nout, checked on the host), so each
+  // product lands in its accumulator directly
   df acc[NOUT][N1];
 #pragma unroll
-  for (int j = 0; j < NOUT; ++j)
+  for (int j = 0; j < NOUT; ++j) {
+    if (valid && j < P.nterm) {
+      elem_product_df<NORD, false>(S.es[j], S.ea[j], S.e1[j], S.has1[j], tin[P.t_src[j]] + NORD * te * TW + tw, TW,
+                                   acc[j]);
+    } else {
 #pragma unroll
-    for (int q = 0; q < N1; ++q) acc[j][q] = df{0.0f, 0.0f};
-  if (valid) {
-    for (int t = 0; t < P.nterm; ++t) {
-      df y[N1];
-      const int src = P.t_src[t];
-      elem_product_df<NORD, false>(S.es[t], S.ea[t], S.e1[t], S.has1[t], tin[src] + NORD * te * TW + tw, TW,
-                                   P.in_df[src] != 0, y);
-      const int d = P.t_dst[t];
-#pragma unroll
-      for (int j = 0; j < NOUT; ++j)
-        if (j == d)
-#pragma unroll
-          for (int q = 0; q < N1; ++q) acc[j][q] = df_add(acc[j][q], y[q]);
+      for (int q = 0; q < N1; ++q) acc[j][q] = df{0.0f, 0.0f};
     }
   }
 #pragma unroll
@@ -497,15 +498,14 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) acc[j][NORD] = df_add(acc[j][NORD], S.row0[j][threadIdx.x + TW]);
       } else {
-        for (int t = 0; t < P.nterm; ++t) {
-          df y[N1];
-          const int src = P.t_src[t];
-          elem_product_df<NORD, true>(S.es[t], S.ea[t], S.e1[t], S.has1[t], tin[src] + NORD * (te + 1) * TW + tw,
-                                      TW, P.in_df[src] != 0, y);
-          const int d = P.t_dst[t];
 #pragma unroll
-          for (int j = 0; j < NOUT; ++j)
-            if (j == d) acc[j][NORD] = df_add(acc[j][NORD], y[0]);
+        for (int j = 0; j < NOUT; ++j) {
+          if (j < P.nterm) {
+            df y[N1];
+            elem_product_df<NORD, true>(S.es[j], S.ea[j], S.e1[j], S.has1[j],
+                                        tin[P.t_src[j]] + NORD * (te + 1) * TW + tw, TW, y);
+            acc[j][NORD] = df_add(acc[j][NORD], y[0]);
+          }
         }
       }
     }

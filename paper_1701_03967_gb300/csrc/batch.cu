@@ -660,7 +660,7 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
           psteps[p].push_back(bs);
         }
       } else {
-        if (op.ap.nout > 2 || op.ap.dotv || op.ap.norms) {
+        if (op.ap.nout > 2 || op.ap.dotv || op.ap.norms || (op.ap.df && !apply_df_form_ok(op.ap))) {
           free_batch(b);
           return batch_fail(FEM_FFT_ERR_ARG, "batch: unsupported apply form");
         }

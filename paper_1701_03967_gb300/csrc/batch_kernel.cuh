@@ -128,7 +128,7 @@ __device__ __forceinline__ void batch_apply_item(const ApplyParams& P, int TW, l
 
 template <int NORD, int NOUT>
 __device__ __forceinline__ void batch_apply_item_df(const ApplyParams& P, int TW, long long b0, long long b1,
-                                                    unsigned char* smem, uint2* tiles) {
+                                                    unsigned char* smem, float2* tiles) {
   auto& S = *reinterpret_cast<ApplySmemDF<NORD, NOUT, kBatchThreads>*>(smem);
   apply_stage_mats_df<NORD, NOUT, kBatchThreads>(P, S);
   for (long long b = b0; b < b1; ++b) {
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchCtasPerSm) batch_kernel(B
     for (int i = threadIdx.x; i < (int)(sizeof(ApplyParams) / sizeof(int)); i += blockDim.x) dst[i] = __ldg(&src[i]);
     __syncthreads();
     if (ap->df) {
-      uint2* tiles = reinterpret_cast<uint2*>(smem + batch_apply_smem<NORD>());
+      float2* tiles = reinterpret_cast<float2*>(smem + batch_apply_smem<NORD>());
       if (mode <= 1) batch_apply_item_df<NORD, 1>(*ap, S.TW, u0, u1, smem, tiles);
       else batch_apply_item_df<NORD, 2>(*ap, S.TW, u0, u1, smem, tiles);
     } else {

@@ -15,9 +15,10 @@
 // operand's 2^-48).
 //
 // split_f64 converts a float64 value to hi + lo with integer operations
-// only (no float64 instruction): hi takes the top 24 significant bits
-// (truncated), lo the next 29 bits rounded to 24.  Values below 2^-126 in
-// magnitude map to zero; the fields here are many orders of magnitude larger.
+// only (no float64 instruction, not even on the overflow path): hi takes the
+// top 24 significant bits (truncated), lo the next 29 bits rounded to 24.
+// Values below 2^-126 in magnitude map to zero; the fields here are many
+// orders of magnitude larger.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -86,7 +87,10 @@ __device__ __forceinline__ df split_f64(double x) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const unsigned hi32 = (unsigned)(bits >> 32);
   const int e = (int)((hi32 >> 20) & 0x7ffu);   // biased float64 exponent
-  if (e > 1150) return {__double2float_rn(x), 0.0f};   // beyond the float range: inf or nan, as float does
+  if (e > 1150) {   // |x| >= 2^128 rounds to infinity in float; nan stays nan
+    const bool nan = e == 2047 && (bits & 0x000fffffffffffffull) != 0;
+    return {__uint_as_float((hi32 & 0x80000000u) | 0x7f800000u | (nan ? 0x00400000u : 0u)), 0.0f};
+  }
   if (e < 897) return {0.0f, 0.0f};                   // |x| < 2^-126
   const unsigned sign = hi32 & 0x80000000u;
   const unsigned long long mant = bits & 0x000fffffffffffffull;

@@ -51,6 +51,13 @@ struct ApplyParams {
   long long plane;
 };
 
+// The double-float apply handles one or two outputs, term t writing output t.
+inline bool apply_df_form_ok(const ApplyParams& P) {
+  if (P.dotv || P.nout < 1 || P.nout > 2 || P.nterm != P.nout) return false;
+  for (int t = 0; t < P.nterm; ++t)
+    if (P.t_dst[t] != t) return false;
+  return true;
+}
 int launch_apply(const ApplyParams& P, cudaStream_t s);
 
 // Algorithm (b) along axis 0 (band.cu): the 1D problems
