@@ -460,15 +460,13 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
   const int wvalid = (int)min((long long)TW, P.inner - w0);
   // stage every input the block uses
   float2* tin[kApplyMaxIn];
-  {
-    int k = 0;
-    for (int i = 0; i < kApplyMaxIn; ++i) {
-      tin[i] = tiles + (size_t)k * rows * TW;
-      if (P.in[i]) {
-        stage_input_df<NC>(P.in[i], P.in_df[i] != 0, plane, o * (long long)P.M * P.inner + w0, P.inner, g0, rows,
-                           TW, wvalid, P.M, tin[i]);
-        ++k;
-      }
+  int nstaged = 0;
+  for (int i = 0; i < kApplyMaxIn; ++i) {
+    tin[i] = tiles + (size_t)nstaged * rows * TW;
+    if (P.in[i]) {
+      stage_input_df<NC>(P.in[i], P.in_df[i] != 0, plane, o * (long long)P.M * P.inner + w0, P.inner, g0, rows, TW,
+                         wvalid, P.M, tin[i]);
+      ++nstaged;
     }
   }
   __syncthreads();
@@ -509,6 +507,49 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
         }
       }
     }
+  }
+  // Plain double-float outputs of a block narrower than a warp (TW < 32:
+  // the contiguous axis has TW = 1) leave through the input tiles, which
+  // are free now: written per element, stored row by row so that a warp's
+  // stores are contiguous (a thread's own rows are TW * inner apart).
+  const int orows = NORD * TE;
+  const bool stage_out = TW < 32 && !P.base && !P.addend && !P.out0_f32 && P.nout * orows <= nstaged * rows;
+  if (stage_out) {
+    __syncthreads();   // every staged input has been read
+    if (valid) {
+      const int nrow = e < K - 1 ? NORD : NORD - 1;
+#pragma unroll
+      for (int r = 0; r < NORD; ++r) {
+        if (r >= nrow) break;
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j)
+          if (j < P.nout)
+            tiles[((size_t)j * orows + NORD * te + r) * TW + tw] = make_float2(acc[j][r + 1].hi, acc[j][r + 1].lo);
+      }
+    }
+    __syncthreads();
+    const int g_first = NORD * (int)(et * TE);
+    const int rows_out = min(orows, P.M - g_first);
+    const int tw_shift = __ffs(TW) - 1;
+    const long long base_off = o * (long long)P.M * P.inner + (long long)g_first * P.inner + w0;
+    for (int i = threadIdx.x; i < rows_out * TW; i += blockDim.x) {
+      const int rho = i >> tw_shift, c = i & (TW - 1);
+      if (c < wvalid) {
+        const long long off = base_off + (long long)rho * P.inner + c;
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j)
+          if (j < P.nout) {
+            const float2 v = tiles[(size_t)j * orows * TW + i];
+            float* f = reinterpret_cast<float*>(P.out[j]);
+            f[off] = v.x;
+            f[plane + off] = v.y;
+          }
+      }
+    }
+    return;
+  }
+  if (valid) {
+    const bool has_node = e < K - 1;
     const int nrow = has_node ? NORD : NORD - 1;
 #pragma unroll
     for (int r = 0; r < NORD; ++r) {
