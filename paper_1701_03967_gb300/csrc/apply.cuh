@@ -551,6 +551,26 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
   if (valid) {
     const bool has_node = e < K - 1;
     const int nrow = has_node ? NORD : NORD - 1;
+    // every row's addend and base values are loaded before the first store:
+    // issued inside the store loop, the float loads of a row could not pass
+    // the float stores of the rows before it and each row waited on memory
+    if (NOUT == 1 && P.addend) {
+      float2 ad[NORD];
+#pragma unroll
+      for (int r = 0; r < NORD; ++r) {
+        const long long off = line + (long long)(NORD * e + min(r, nrow - 1)) * P.inner;
+        const float* a = reinterpret_cast<const float*>(P.addend);
+        ad[r] = make_float2(ld_f32<NC>(a + off), ld_f32<NC>(a + plane + off));
+      }
+#pragma unroll
+      for (int r = 0; r < NORD; ++r) acc[0][r + 1] = df_add(acc[0][r + 1], df{ad[r].x, ad[r].y});
+    }
+    double bv[NORD];
+    if (NOUT == 1 && P.base) {
+#pragma unroll
+      for (int r = 0; r < NORD; ++r)
+        bv[r] = ld_f64<NC>(&P.base[line + (long long)(NORD * e + min(r, nrow - 1)) * P.inner]);
+    }
 #pragma unroll
     for (int r = 0; r < NORD; ++r) {
       if (r >= nrow) break;
@@ -559,9 +579,8 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
       for (int j = 0; j < NOUT; ++j) {
         if (j < P.nout) {
           df v = acc[j][r + 1];
-          if (j == 0 && P.addend) v = df_add(v, ld_df<NC>(P.addend, true, plane, off));
-          if (j == 0 && P.base) {
-            const df b = split_f64(ld_f64<NC>(&P.base[off]));
+          if (NOUT == 1 && P.base) {
+            const df b = split_f64(bv[r]);
             const float rv = df_to_float(df_sub(b, v));
             rr = fmaf(rv, rv, rr);
             bb = fmaf(b.hi, b.hi, bb);

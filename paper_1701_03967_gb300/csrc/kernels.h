@@ -51,9 +51,11 @@ struct ApplyParams {
   long long plane;
 };
 
-// The double-float apply handles one or two outputs, term t writing output t.
+// The double-float apply handles one or two outputs, term t writing output t;
+// an addend, a residual base or a float32 output only with one output.
 inline bool apply_df_form_ok(const ApplyParams& P) {
   if (P.dotv || P.nout < 1 || P.nout > 2 || P.nterm != P.nout) return false;
+  if (P.nout > 1 && (P.addend || P.base || P.out0_f32)) return false;
   for (int t = 0; t < P.nterm; ++t)
     if (P.t_dst[t] != t) return false;
   return true;
