@@ -132,9 +132,10 @@ def time_steps(torch, fn, steps, warmup, barrier=None):
 
 
 # DRAM bytes (read + write) per DOF of one double-float residual apply, the
-# average of the three launches of a 2D n=9 residual chain, from ncu
-# (profiles/apply_kernel_df_2d_n9_K512.md: 573.2 MB per launch at 21.2 M DOF)
-APPLY_DF_TRAFFIC_PER_DOF_2D_N9 = 573.2e6 / 21224449
+# average of the three launches of a 2D n=9 residual chain, from one ncu
+# capture of the K=512x512 case (510.6 MB per launch at 21.2 M DOF), scaled
+# by the unknowns
+APPLY_DF_TRAFFIC_PER_DOF_2D_N9 = 510.6e6 / 21224449
 
 
 def roofline(prof, steps, peaks, wl=None):
@@ -252,9 +253,10 @@ def run_other_workloads(torch, args, barrier):
     """The other configurations, timed like the headline (device-resident
     N(0,1) right-hand sides, CUDA events): the n = 1..9 sweep of the 2D
     workload at K = 1024 x 1024, the 3D workloads n=9 K=64^3 and n=4 K=128^3
-    (mixed and FP64), algorithm (b) on the 2D n=9 and 3D n=9 workloads, and
+    (mixed and FP64), algorithm (b) on the 2D n=9 and 3D n=9 workloads,
     one differentiation step (forward solve + adjoint solve + coefficient
-    gradients) of 3D n=5 K=64^3 in mixed precision."""
+    gradients) of 3D n=5 K=64^3 in mixed precision, and the 1D transform
+    sweep (n = 5, K = 2^5 ...)."""
     from paper_1701_03967_gb300 import Plan, fem_solve
     g = torch.Generator(device="cuda").manual_seed(1701)
     steps = max(2, args.steps // 2)
@@ -303,7 +305,50 @@ def run_other_workloads(torch, args, barrier):
     ms = time_steps(torch, grad_step, steps, args.warmup, barrier)
     res["grad_3d_n5_K64"] = {"ms": ms, "dof": pl.dof, "note": "loss.backward() of ||u - u_t||^2, u = L(a, c)^-1 f"}
     pl.close()
+    torch.cuda.empty_cache()
+    res["transform_1d_n5"] = transform_sweep(torch, args, barrier, g)
     return res
+
+
+def transform_sweep(torch, args, barrier, g, n=5):
+    """The 1D transform timing of Section 5 (direct FC_n and inverse F_n
+    transforms, n = 5, K from 2^5 up, powers of two and composites): float64
+    transforms of a batch of pencils of 2^24 unknowns in all, reported per
+    transform.  K whose pencil does not fit one CTA's shared memory is listed
+    as refused (the kernels keep a whole pencil on chip)."""
+    from paper_1701_03967_gb300 import FemFftError, Plan
+    steps = max(2, args.steps // 2)
+    out = {}
+    Ks = [2 ** p for p in range(5, 15)] + [3 * 2 ** p for p in range(4, 13)]
+    for K in sorted(Ks):
+        M = n * K - 1
+        nrhs = max(1, (1 << 24) // M)
+        pl = None
+        try:
+            pl = Plan(n, (K,), None, None, 0.0, precision="fp64", max_nrhs=nrhs)
+            y = torch.randn(nrhs, M, dtype=torch.float64, device="cuda", generator=g)
+            c = torch.empty_like(y)
+            w = torch.empty_like(y)
+            pl.forward(y, out=c)
+            pl.inverse(c, out=w)
+        except FemFftError as e:   # the pass planner refuses a pencil larger than a CTA's shared memory
+            out[str(K)] = {"refused": str(e)[:120]}
+            if pl is not None:
+                pl.close()
+            continue
+        ms_f = time_steps(torch, lambda: pl.forward(y, out=c), steps, args.warmup, barrier)
+        ms_i = time_steps(torch, lambda: pl.inverse(c, out=w), steps, args.warmup, barrier)
+        # the direct transform expands calC^-1 y (Theorem 2), so the round trip
+        # of the mass product returns the field itself
+        pl.forward(pl.apply_mass(y), out=c)
+        pl.inverse(c, out=w)
+        rel = float(torch.linalg.vector_norm(w - y) / torch.linalg.vector_norm(y))
+        out[str(K)] = {"M": M, "pencils": nrhs, "forward_us": ms_f * 1e3 / nrhs, "inverse_us": ms_i * 1e3 / nrhs,
+                       "forward_dof_per_s": nrhs * M / (ms_f * 1e-3), "inverse_dof_per_s": nrhs * M / (ms_i * 1e-3),
+                       "mass_roundtrip_rel_err": rel}
+        pl.close()
+        del y, c, w
+    return out
 
 
 def workload_config(wl, args, ws):
