@@ -219,10 +219,19 @@ def run_batched(torch, args, barrier):
     ms_64 = time_steps(torch, seq64, max(2, args.steps // 2), args.warmup, barrier)
     rel = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
     units = float(batch.total_len)
+    # the same mixed plans launched one problem after another (what the batch replaces)
+    umx = torch.empty_like(b)
+    mviews = list(zip(plans, batch.views(b), batch.views(umx)))
+
+    def seq_mixed():
+        for pl, x, y in mviews:
+            pl.solve(x, out=y)
+    ms_mx = time_steps(torch, seq_mixed, max(2, args.steps // 2), args.warmup, barrier)
     out = {"workload": "256 problems, N in {2,3}, n 2..8, K_i in {16,32,48,96,128,384,512}, 1-8 rhs",
            "dof_x_rhs": batch.total_len, "steps": batch.n_steps, "items": batch.n_items,
            "value": units / (ms_b * 1e-3), "unit": "DOF/s", "ms_per_solve": ms_b,
            "fp64_sequential": {"value": units / (ms_64 * 1e-3), "ms_per_solve": ms_64},
+           "mixed_sequential": {"value": units / (ms_mx * 1e-3), "ms_per_solve": ms_mx},
            "rel_vs_fp64": rel, "create_s": t_create, "launches_per_solve": len({s["n"] for s in specs})}
     batch.close()
     # the same problems with every plan on algorithm (b), batched and sequential FP64
