@@ -16,7 +16,7 @@ import ctypes
 from . import _lib
 from ._lib import FEM_FFT_FP64, FEM_FFT_MIXED, FemFftError  # noqa: F401
 
-__all__ = ["Plan", "Batch", "HeatStepper", "FemFftError", "solve", "lib_path", "fem_solve"]
+__all__ = ["Plan", "Batch", "HeatStepper", "HostSolveStream", "FemFftError", "solve", "lib_path", "fem_solve"]
 
 lib_path = _lib.LIB_PATH
 
@@ -350,6 +350,76 @@ class HeatStepper:
 
     def close(self):
         self.plan.close()
+
+
+class HostSolveStream:
+    """Solves of right-hand sides held in pinned host memory, pipelined: the
+    upload of a right-hand side and the download of a solution run on their
+    own CUDA streams while other solves run on the compute stream, over
+    ``depth`` device buffer pairs.  ``submit(b_host, u_host)`` queues
+    b -> device, u = L^-1 b (``Plan.solve``), u -> u_host and returns at once;
+    ``wait()`` makes the compute stream wait for every queued download, and
+    ``synchronize()`` waits on the host.  Host tensors must stay alive and
+    unmodified until their transfer has completed (pinned float64 tensors of
+    the plan's field shape, or (nrhs,) + that shape)."""
+
+    def __init__(self, plan, nrhs=1, depth=2):
+        torch = _torch()
+        if depth < 1:
+            raise ValueError("depth must be >= 1")
+        self.plan = plan
+        shape = plan.M if nrhs == 1 else (int(nrhs),) + tuple(plan.M)
+        dev = plan._torch_device
+        self._b = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(depth)]
+        self._u = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(depth)]
+        self._h2d = torch.cuda.Stream(device=dev)
+        self._d2h = torch.cuda.Stream(device=dev)
+        self._solved = [None] * depth   # solve that last read b[i] and wrote u[i]
+        self._down = [None] * depth     # download that last read u[i]
+        self._k = 0
+
+    def submit(self, b_host, u_host, stream=None):
+        torch = _torch()
+        comp = stream if stream is not None else torch.cuda.current_stream()
+        i = self._k % len(self._b)
+        if b_host.shape != self._b[i].shape or u_host.shape != self._u[i].shape:
+            raise ValueError("host tensors must have the stream's field shape")
+        up = torch.cuda.Event()
+        with torch.cuda.stream(self._h2d):
+            if self._solved[i] is not None:
+                self._h2d.wait_event(self._solved[i])   # b[i] is no longer read
+            self._b[i].copy_(b_host, non_blocking=True)
+            up.record(self._h2d)
+        comp.wait_event(up)
+        if self._down[i] is not None:
+            comp.wait_event(self._down[i])              # u[i] has been read back
+        self.plan.solve(self._b[i], out=self._u[i], stream=comp)
+        solved = torch.cuda.Event()
+        solved.record(comp)
+        self._solved[i] = solved
+        down = torch.cuda.Event()
+        with torch.cuda.stream(self._d2h):
+            self._d2h.wait_event(solved)
+            u_host.copy_(self._u[i], non_blocking=True)
+            down.record(self._d2h)
+        self._down[i] = down
+        self._k += 1
+
+    def start_after(self, event):
+        """Later uploads wait for ``event`` (e.g. the start of a timed region)."""
+        self._h2d.wait_event(event)
+
+    def wait(self, stream=None):
+        torch = _torch()
+        comp = stream if stream is not None else torch.cuda.current_stream()
+        for ev in self._down:
+            if ev is not None:
+                comp.wait_event(ev)
+
+    def synchronize(self):
+        for ev in self._down:
+            if ev is not None:
+                ev.synchronize()
 
 
 def batch_order(nsteps, work=None):
