@@ -129,6 +129,25 @@ def assemble(n, K):
     return calA, calC
 
 
+def assemble_full(n, K):
+    """Dense h-free operators of the space with the two boundary nodes kept,
+    (nK+1) x (nK+1): the same element blocks summed over the K elements, with
+    fine index m = n e + q (0..nK) for local node q of element e (0-based).
+    Rows/columns 1..nK-1 are ``assemble``'s; rows 0 and nK and the columns of
+    the boundary nodes carry the coupling that Dirichlet data enter through
+    (Section 4: u = g on the boundary, f^h modified by the boundary values)."""
+    A, C = reference_matrices(n)
+    M = n * K + 1
+    fA = np.zeros((M, M))
+    fC = np.zeros((M, M))
+    for e in range(K):
+        for q in range(n + 1):
+            for r in range(n + 1):
+                fA[n * e + q, n * e + r] += A[q, r]
+                fC[n * e + q, n * e + r] += C[q, r]
+    return fA, fC
+
+
 def assemble_sparse(n, K):
     """The same (calA, calC) as ``assemble``, as scipy CSR matrices."""
     import scipy.sparse

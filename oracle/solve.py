@@ -211,6 +211,44 @@ def solve_b(prob, b):
     return v[0] if single else v
 
 
+def dirichlet_rhs(prob, g):
+    """d = (L_full G) restricted to the interior nodes, where G is the FEM
+    function with the boundary values of ``g`` at the boundary nodes and 0
+    inside, and L_full the operator of Section 4 on the space that keeps the
+    boundary nodes (``fem1d.assemble_full`` on every axis).  ``g`` has shape
+    (M_1+2, ..., M_N+2) or (nrhs,) + that (the fine grid extended by the
+    boundary node at each end); only its boundary entries are used.  The
+    solution with u = g on the boundary is u = L^{-1}(f^h - d) inside
+    (the Dirichlet condition of Section 4 with non-zero data: u - G lies in
+    the space with zero boundary values)."""
+    x = np.array(g, dtype=np.float64)
+    ext = tuple(m + 2 for m in prob.M)
+    single = x.shape == ext
+    if single:
+        x = x[None]
+    if x.shape[1:] != ext:
+        raise ValueError(f"g has shape {x.shape}, expected {ext} or (nrhs,)+{ext}")
+    inner = (slice(None),) + (slice(1, -1),) * prob.N
+    x[inner] = 0.0
+    full = [fem1d.assemble_full(prob.n, k) for k in prob.K]
+    out = np.zeros_like(x)
+    for i in range(prob.N + 1):
+        t = x
+        for j in range(prob.N):
+            fA, fC = full[j]
+            t = _axis_apply(t, fA if j == i else fC, j + 1)
+        coef = prob.c if i == prob.N else prob.a[i] * prob.s[i]
+        out += coef * t
+    d = out[inner]
+    return d[0] if single else d
+
+
+def solve_dirichlet(prob, b, g):
+    """Interior values of the solution with the boundary values of ``g``:
+    L^{-1} (b - dirichlet_rhs(prob, g))."""
+    return solve(prob, np.asarray(b, dtype=np.float64) - dirichlet_rhs(prob, g))
+
+
 def mass_apply(prob, u):
     """(prod_j calC_j) u: the mass operator of the N-D space (Section 2, the
     global 1D mass matrices, in tensor products as in Section 4), by

@@ -339,3 +339,62 @@ def test_planted_mistakes_are_caught(monkeypatch):
     assert np.max(np.abs(R)) > 1e-3
     monkeypatch.setattr(fem1d, "dispersion_roots", orig_roots)
     solve._BASIS.clear()
+
+
+def test_full_assembly_structure():
+    """The operators with the boundary nodes kept: their interior block is the
+    Dirichlet operator, the stiffness annihilates constants (the constant
+    function lies in the full space and has zero derivative) and the mass
+    entries sum to the measure of (0, K) in reference units, 2K."""
+    for n, K in [(1, 3), (2, 4), (5, 3)]:
+        fA, fC = fem1d.assemble_full(n, K)
+        A, C = fem1d.assemble(n, K)
+        assert np.allclose(fA[1:-1, 1:-1], A, atol=1e-14) and np.allclose(fC[1:-1, 1:-1], C, atol=1e-14)
+        assert np.max(np.abs(fA.sum(axis=1))) < 1e-12
+        assert abs(fC.sum() - 2.0 * K) < 1e-12
+
+
+DIRICHLET_CASES = [dict(n=2, K=(3, 4), X=(1.0, 1.5), a=(1.3, 0.7), c=0.4),
+                   dict(n=3, K=(2, 3, 2), X=(1.0, 0.8, 1.2), a=(0.9, 1.1, 2.0), c=0.0),
+                   dict(n=4, K=(5,), X=(2.0,), a=(2.0,), c=1.5)]
+
+
+@pytest.mark.parametrize("case", DIRICHLET_CASES, ids=[f"n{c['n']}_{len(c['K'])}d" for c in DIRICHLET_CASES])
+def test_dirichlet_data_reproduce_polynomials(case):
+    """Section 4 with non-zero boundary values: when the exact solution is a
+    polynomial of degree <= n in every variable it lies in the FEM space, so
+    the Galerkin solution equals it; the load vector of its right-hand side
+    -sum a_i u_ii + c u is exact with (n+1)-point Gauss (Section 5).  So the
+    solve with the boundary correction must return u at every interior node,
+    whatever the coefficients; a dropped term, a wrong sign or a wrong
+    coupling in the correction breaks the equality."""
+    n, N = case["n"], len(case["K"])
+    prob = solve.Problem(n, case["K"], case["X"], case["a"], case["c"])
+    rng = np.random.default_rng(11)
+    P = [np.polynomial.Polynomial(rng.uniform(-1, 1, n + 1)) for _ in range(N)]
+    Qp = [np.polynomial.Polynomial(rng.uniform(-1, 1, n + 1)) for _ in range(N)]
+
+    def u(*x):
+        prod = np.ones_like(x[0])
+        for i in range(N):
+            prod = prod * P[i](x[i])
+        return prod + sum(Qp[i](x[i]) for i in range(N))
+
+    def f(*x):
+        out = prob.c * u(*x)
+        for i in range(N):
+            t = P[i].deriv(2)(x[i])
+            for j in range(N):
+                if j != i:
+                    t = t * P[j](x[j])
+            out = out - prob.a[i] * (t + Qp[i].deriv(2)(x[i]))
+        return out
+
+    b = harness.load_vector(prob, f)
+    ext_grid = [np.arange(prob.M[i] + 2) * prob.h[i] / n for i in range(N)]
+    g = u(*np.meshgrid(*ext_grid, indexing="ij"))
+    got = solve.solve_dirichlet(prob, b, g)
+    want = harness.nodal_values(prob, u)
+    assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
+    # without the correction the boundary values are lost
+    assert np.max(np.abs(solve.solve(prob, b) - want)) > 1e-3 * np.max(np.abs(want))
