@@ -138,6 +138,25 @@ int fem_fft_apply(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrh
 int fem_fft_apply_mass(fem_fft_plan plan, const double* d_u, double* d_b, int64_t nrhs, void* stream);
 
 /*
+ * fem_fft_dirichlet_rhs -- non-zero Dirichlet data (Section 4, u = g on the
+ * boundary instead of 0): d_b -= L_full G on the interior nodes, where G is
+ * the FEM function with g's values at the boundary nodes and 0 inside and
+ * L_full the operator of Section 4 on the space that keeps the boundary
+ * nodes.  Then fem_fft_solve of the corrected d_b gives the interior values
+ * of the solution (u - G has zero boundary values).
+ *   d_g  nrhs fields extended by the boundary node at each end of every axis:
+ *        [nrhs][M_1 + 2]...[M_N + 2] float64, C order, fine index m of axis i
+ *        (the node at x_i = m h_i / n, m = 0 .. n K_i) at position m; only the
+ *        boundary entries are read (the interior is taken as 0)
+ *   d_b  [nrhs][M_1]...[M_N] float64, corrected in place (typically f^h)
+ * Float64 operator products on the extended fields; temporaries of 2, 4 or
+ * 5 extended fields (N = 1, 2, 3) come from the stream-ordered allocator
+ * (cudaMallocAsync) and are released on the stream.  FEM_FFT_ERR_OOM if they
+ * cannot be had.  Asynchronous on stream.
+ */
+int fem_fft_dirichlet_rhs(fem_fft_plan plan, const double* d_g, double* d_b, int64_t nrhs, void* stream);
+
+/*
  * fem_fft_set_algorithm -- the solver of fem_fft_solve (N >= 2):
  * FEM_FFT_ALGO_A (default) is algorithm (a) of Section 4 (FC_n / F_n
  * transforms along every axis and the spectral division); FEM_FFT_ALGO_B is

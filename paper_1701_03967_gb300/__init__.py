@@ -112,6 +112,30 @@ class Plan:
                    "fem_fft_apply_mass")
         return b
 
+    def dirichlet_rhs(self, g, b, stream=None):
+        """b -= L_full G in place (fem_fft_dirichlet_rhs): g holds the boundary
+        values on the grid extended by the boundary node at each end of every
+        axis, shape (M_1+2, ..., M_N+2) or (nrhs,) + that; b is a field of
+        the plan's shape with as many right-hand sides."""
+        torch = _torch()
+        nrhs = self._field(b, "b")
+        ext = tuple(m + 2 for m in self.M)
+        want = ext if (nrhs == 1 and tuple(b.shape) == self.M) else (nrhs,) + ext
+        if not isinstance(g, torch.Tensor) or not g.is_cuda or g.dtype != torch.float64 or not g.is_contiguous():
+            raise TypeError("g must be a contiguous CUDA float64 tensor")
+        if tuple(g.shape) != want:
+            raise ValueError(f"g has shape {tuple(g.shape)}, expected {want}")
+        _lib.check(_lib.lib().fem_fft_dirichlet_rhs(self._h, g.data_ptr(), b.data_ptr(), nrhs, self._stream(stream)),
+                   "fem_fft_dirichlet_rhs")
+        return b
+
+    def solve_dirichlet(self, f, g, out=None, stream=None):
+        """Interior values of the solution with u = g on the boundary:
+        L^{-1} (f - L_full G) (Section 4 with non-zero Dirichlet data)."""
+        rhs = f.clone()
+        self.dirichlet_rhs(g, rhs, stream=stream)
+        return self.solve(rhs, out=out, stream=stream)
+
     def forward(self, y, out=None, stream=None):
         """Direct FC_n coefficients along every axis (float64)."""
         nrhs = self._field(y, "y")

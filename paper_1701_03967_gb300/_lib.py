@@ -44,6 +44,7 @@ def lib():
         "fem_fft_solve": ([vp, vp, vp, i64, vp], i32),
         "fem_fft_apply": ([vp, vp, vp, i64, vp], i32),
         "fem_fft_apply_mass": ([vp, vp, vp, i64, vp], i32),
+        "fem_fft_dirichlet_rhs": ([vp, vp, vp, i64, vp], i32),
         "fem_fft_set_refinement": ([vp, f64, i32], i32),
         "fem_fft_plan_tune": ([vp, vp], i32),
         "fem_fft_set_algorithm": ([vp, i32, vp], i32),

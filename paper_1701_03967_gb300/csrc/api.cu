@@ -714,6 +714,107 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
   return FEM_FFT_OK;
 }
 
+// b -= L_full G on the interior nodes, G the boundary values of g (fields
+// extended by the boundary node at each end of every axis): Section 4 with
+// u = g on the boundary, f^h corrected by the data.  The chain of
+// operator_chain (stiffness factors on G itself, mass factors after them),
+// every launch on extended fields (gofs = 1) so that each product keeps the
+// boundary positions of the other axes; the result's interior is subtracted
+// from b.  Temporaries come from the stream-ordered allocator.
+int dirichlet_chain(fem_fft_plan p, const double* g, double* b, long long nrhs, cudaStream_t s) {
+  const int N = p->N, n1 = p->n + 1;
+  const std::vector<double>& A = p->Aref;
+  const std::vector<double>& C = p->Cref;
+  double s_[kMaxN];
+  long long Mx[kMaxN];
+  size_t ext = 1;
+  for (int i = 0; i < N; ++i) {
+    s_[i] = p->a[i] * 4.0 * p->K[i] * p->K[i] / (p->X[i] * p->X[i]);
+    Mx[i] = p->M[i];
+    ext *= (size_t)(p->M[i] + 2);
+  }
+  const size_t field = ext * (size_t)nrhs;
+  const int nbuf = N == 1 ? 2 : (N == 2 ? 4 : 5);
+  double* buf = nullptr;
+  if (cudaMallocAsync(&buf, field * nbuf * sizeof(double), s) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("dirichlet: temporaries");
+    return FEM_FFT_ERR_OOM;
+  }
+  int rc = FEM_FFT_OK;
+  double* Gz = buf;
+  double* X = buf + field;
+  double* Y = X + field;
+  double* Z = Y + field;
+  double* W = Z + field;
+  auto ext_base = [&](int axis) {
+    ApplyParams P = apply_base(p, axis, nrhs);
+    long long outer = nrhs, inner = 1;
+    for (int j = 0; j < axis; ++j) outer *= p->M[j] + 2;
+    for (int j = axis + 1; j < N; ++j) inner *= p->M[j] + 2;
+    P.outer = outer;
+    P.inner = inner;
+    P.gofs = 1;
+    return P;
+  };
+  auto one = [&](int axis, const double* in, double* o, const std::vector<double>& E, double alpha,
+                 const std::vector<double>* E2, double beta) {
+    ApplyParams P = ext_base(axis);
+    P.in[0] = in;
+    P.nterm = 1;
+    P.nout = 1;
+    P.out[0] = o;
+    set_mat(P, 0, E, alpha, E2, beta, n1, p->Aref, p->Crow);
+    return P;
+  };
+  auto two = [&](int axis, const double* in0, double* o0, const double* in1, double* o1, double s1) {
+    ApplyParams P = ext_base(axis);   // o0 = C in0, o1 = s1 A in1
+    P.in[0] = in0;
+    P.in[1] = in1;
+    P.nterm = 2;
+    P.nout = 2;
+    P.out[0] = o0;
+    P.out[1] = o1;
+    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    P.t_src[0] = 0; P.t_dst[0] = 0;
+    set_mat(P, 1, A, s1, nullptr, 0.0, n1, p->Aref, p->Crow);
+    P.t_src[1] = 1; P.t_dst[1] = 1;
+    return P;
+  };
+  auto run = [&](const ApplyParams& P) {
+    if (rc) return;
+    const int e = apply_launch(p, P, s);
+    if (e) rc = cuda_fail((cudaError_t)e, "dirichlet apply");
+  };
+  double* T = X;
+  int e = cudaMemsetAsync(buf, 0, field * nbuf * sizeof(double), s);
+  if (!e) e = launch_boundary_only(g, Gz, nrhs, N, Mx, s);
+  if (e) rc = cuda_fail((cudaError_t)e, "dirichlet boundary data");
+  run(one(0, Gz, X, A, s_[0], &C, p->c));               // X = E_1 G
+  if (N >= 2) run(two(1, X, Y, Gz, Z, s_[1]));          // Y = C_2 X, Z = a2 s2 A_2 G
+  if (N == 2) {
+    ApplyParams P = one(0, Z, X, C, 1.0, nullptr, 0.0);  // T = Y + C_1 Z
+    P.addend = Y;
+    run(P);
+  } else if (N == 3) {
+    ApplyParams P = one(0, Z, Y, C, 1.0, nullptr, 0.0);  // Y += C_1 Z
+    P.addend = Y;
+    run(P);
+    run(two(2, Y, W, Gz, X, s_[2]));                     // W = C_3 Y, X = a3 s3 A_3 G
+    run(one(1, X, Z, C, 1.0, nullptr, 0.0));             // Z = C_2 X
+    ApplyParams Q = one(0, Z, Y, C, 1.0, nullptr, 0.0);  // T = W + C_1 Z
+    Q.addend = W;
+    run(Q);
+    T = Y;
+  }
+  if (!rc) {
+    e = launch_subtract_interior(b, T, nrhs, N, Mx, s);
+    if (e) rc = cuda_fail((cudaError_t)e, "dirichlet subtract");
+  }
+  cudaFreeAsync(buf, s);
+  return rc;
+}
+
 // out = (prod_i calC_i) u: one mass application per axis, through the
 // temporaries (float64).
 int mass_chain(fem_fft_plan p, const double* u, long long nrhs, double* out, cudaStream_t s) {
@@ -1133,6 +1234,12 @@ int fem_fft_apply_mass(fem_fft_plan p, const double* u, double* b, int64_t nrhs,
     if ((rc = mass_chain(p, u + (size_t)r0 * p->dof, cnt, b + (size_t)r0 * p->dof, s))) return rc;
   }
   return FEM_FFT_OK;
+}
+
+int fem_fft_dirichlet_rhs(fem_fft_plan p, const double* g, double* b, int64_t nrhs, void* stream) {
+  if (p && nrhs == 0) return FEM_FFT_OK;
+  if (!p || !g || !b || nrhs < 0) return FEM_FFT_ERR_ARG;
+  return dirichlet_chain(p, g, b, nrhs, (cudaStream_t)stream);
 }
 
 int fem_fft_set_algorithm(fem_fft_plan p, int algo, void* stream) {

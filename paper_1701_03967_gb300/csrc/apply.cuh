@@ -95,13 +95,15 @@ __device__ __forceinline__ double ld_f64(const double* p) {
   return __ldcg(p);
 }
 
+// local nodes of element e; gofs = 1: the field stores the boundary nodes
+// too (fine index g at g + 1), so g = -1 and g = M are read, not zeroed
 template <int NORD, bool NC>
 __device__ __forceinline__ void load_elem(const double* x, long long line, long long inner, int e, int M,
-                                          double (&u)[NORD + 1]) {
+                                          int gofs, double (&u)[NORD + 1]) {
 #pragma unroll
   for (int q = 0; q <= NORD; ++q) {
     const int g = NORD * e + q - 1;
-    u[q] = (g >= 0 && g < M) ? ld_f64<NC>(&x[line + (long long)g * inner]) : 0.0;
+    u[q] = (g >= -gofs && g < M + gofs) ? ld_f64<NC>(&x[line + (long long)(g + gofs) * inner]) : 0.0;
   }
 }
 
@@ -188,7 +190,7 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
   const long long w = wt * TW + tw;
   const int e = (int)(et * TE + te);
   const bool valid = w < P.inner && e < K;
-  const long long line = o * (long long)P.M * P.inner + (valid ? w : 0);
+  const long long line = o * (long long)(P.M + 2 * P.gofs) * P.inner + (valid ? w : 0);
 
   double acc[NOUT][N1];
 #pragma unroll
@@ -198,7 +200,7 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
   if (valid) {
     for (int t = 0; t < P.nterm; ++t) {
       double u[N1], y[N1];
-      load_elem<NORD, NC>(P.in[P.t_src[t]], line, P.inner, e, P.M, u);
+      load_elem<NORD, NC>(P.in[P.t_src[t]], line, P.inner, e, P.M, P.gofs, u);
       elem_product<NORD, false>(S.es[t], S.ea[t], S.e1[t], S.has1[t], u, y);
       const int d = P.t_dst[t];
 #pragma unroll
@@ -223,7 +225,7 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
       } else {
         for (int t = 0; t < P.nterm; ++t) {
           double u[N1], y[N1];
-          load_elem<NORD, NC>(P.in[P.t_src[t]], line, P.inner, e + 1, P.M, u);
+          load_elem<NORD, NC>(P.in[P.t_src[t]], line, P.inner, e + 1, P.M, P.gofs, u);
           elem_product<NORD, true>(S.es[t], S.ea[t], S.e1[t], S.has1[t], u, y);
           const int d = P.t_dst[t];
 #pragma unroll
@@ -236,7 +238,7 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
 #pragma unroll
     for (int r = 0; r < NORD; ++r) {
       if (r >= nrow) break;
-      const long long off = line + (long long)(NORD * e + r) * P.inner;
+      const long long off = line + (long long)(NORD * e + r + P.gofs) * P.inner;
       if (P.dotv) {
         const double lv = ld_f64<NC>(&P.dotv[off]);
 #pragma unroll

@@ -49,6 +49,12 @@ struct ApplyParams {
   int df;
   int in_df[kApplyMaxIn];
   long long plane;
+  // 1: every field of the launch carries the two boundary nodes of the
+  // operated axis (extent M + 2, fine index g stored at g + 1); element
+  // loads read the boundary values there, outputs are the M interior rows.
+  // 0: extent M, boundary values zero.  (outer / inner count the stored
+  // positions of the other axes either way.)
+  int gofs;
 };
 
 // The double-float apply handles one or two outputs, term t writing output t;
@@ -56,11 +62,16 @@ struct ApplyParams {
 inline bool apply_df_form_ok(const ApplyParams& P) {
   if (P.dotv || P.nout < 1 || P.nout > 2 || P.nterm != P.nout) return false;
   if (P.nout > 1 && (P.addend || P.base || P.out0_f32)) return false;
+  if (P.gofs) return false;
   for (int t = 0; t < P.nterm; ++t)
     if (P.t_dst[t] != t) return false;
   return true;
 }
 int launch_apply(const ApplyParams& P, cudaStream_t s);
+// Dirichlet data (dirichlet.cu): fields extended by the boundary node at
+// each end of every axis (extents M_i + 2, C order, nrhs leading)
+int launch_boundary_only(const double* g, double* gz, long long nrhs, int N, const long long* M, cudaStream_t s);
+int launch_subtract_interior(double* b, const double* t, long long nrhs, int N, const long long* M, cudaStream_t s);
 
 // Algorithm (b) along axis 0 (band.cu): the 1D problems
 // [alpha calA + beta_w calC] v = y, one per position w of the later axes, on
