@@ -755,6 +755,10 @@ int dirichlet_chain(fem_fft_plan p, const double* g, double* b, long long nrhs, 
     P.outer = outer;
     P.inner = inner;
     P.gofs = 1;
+    P.bnd = 1;   // the temporaries start at zero (memset below)
+    P.bnd_N = N;
+    P.bnd_axis = axis;
+    for (int j = 0; j < N; ++j) P.bnd_M[j] = p->M[j];
     return P;
   };
   auto one = [&](int axis, const double* in, double* o, const std::vector<double>& E, double alpha,

@@ -47,13 +47,15 @@ int launch_apply(const ApplyParams& P, cudaStream_t s) {
     if (!apply_df_form_ok(P)) return (int)cudaErrorInvalidValue;
     int nin = 0;
     for (int i = 0; i < kApplyMaxIn; ++i) nin += P.in[i] != nullptr;
-    const size_t smem = apply_df_tile_bytes(P.n, TW, kApplyThreads, nin);
+    const int TWd = apply_df_tw(P.inner, P.outer, P.K, kApplyThreads);
+    const long long bdf = apply_df_blocks(P.inner, P.outer, P.K, TWd, kApplyThreads);
+    const size_t smem = apply_df_tile_bytes(P.n, TWd, kApplyThreads, nin);
     int rc = 0;
     switch (P.n) {
 #define FEMFFT_APPLY_DF_CASE(NN)                                                       \
   case NN:                                                                             \
-    rc = P.nout <= 1 ? launch_apply_df<NN, 1>(P, TW, blocks, smem, s)                  \
-                     : launch_apply_df<NN, 2>(P, TW, blocks, smem, s);                 \
+    rc = P.nout <= 1 ? launch_apply_df<NN, 1>(P, TWd, bdf, smem, s)                    \
+                     : launch_apply_df<NN, 2>(P, TWd, bdf, smem, s);                   \
     if (rc) return rc;                                                                 \
     break;
       FEMFFT_APPLY_DF_CASE(1) FEMFFT_APPLY_DF_CASE(2) FEMFFT_APPLY_DF_CASE(3) FEMFFT_APPLY_DF_CASE(4)

@@ -171,6 +171,38 @@ __device__ __forceinline__ void apply_stage_mats(const ApplyParams& P, ApplySmem
   }
 }
 
+// Boundary-layer test of the Dirichlet correction (ApplyParams::bnd): true if
+// one of element e's output rows (its interior rows and its right vertex)
+// can be reached from the boundary of the operated axis -- e = 0, e = K - 1,
+// and e = K - 2, whose right vertex takes row 0 of the last element -- or a
+// stored index of another axis (extended fields: 0 .. M_j + 1) lies within
+// one element of that axis's boundary.  Outside, every product of the chain
+// is zero: each term of it applies one 1D operator per axis to data that is
+// non-zero only at boundary nodes.
+template <typename I>
+__device__ __forceinline__ bool bnd_live_t(const ApplyParams& P, I o, I w, int e) {
+  if (e == 0 || e >= P.K - 2) return true;
+  const I n = (I)P.n;
+  for (int j = P.bnd_N - 1; j > P.bnd_axis; --j) {   // axes after the operated one: w, last axis fastest
+    const I m = (I)P.bnd_M[j];
+    const I i = w % (m + 2);
+    w /= m + 2;
+    if (i <= n || i + n >= m + 1) return true;
+  }
+  for (int j = P.bnd_axis - 1; j >= 0; --j) {        // axes before it: o (right-hand side slowest)
+    const I m = (I)P.bnd_M[j];
+    const I i = o % (m + 2);
+    o /= m + 2;
+    if (i <= n || i + n >= m + 1) return true;
+  }
+  return false;
+}
+// 32-bit divisions when the indices fit (they do for fields below 2^32 values)
+__device__ __forceinline__ bool bnd_live(const ApplyParams& P, long long o, long long w, int e) {
+  if (o < 0xffffffffLL && w < 0xffffffffLL) return bnd_live_t<unsigned>(P, (unsigned)o, (unsigned)w, e);
+  return bnd_live_t<unsigned long long>(P, (unsigned long long)o, (unsigned long long)w, e);
+}
+
 // Block bx of an apply launch: TW consecutive positions of the contiguous
 // axis times NTHREADS / TW consecutive elements of the operated axis.
 template <int NORD, int NOUT, int NTHREADS, bool NC>
@@ -191,13 +223,16 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
   const int e = (int)(et * TE + te);
   const bool valid = w < P.inner && e < K;
   const long long line = o * (long long)(P.M + 2 * P.gofs) * P.inner + (valid ? w : 0);
+  const bool live = valid && (!P.bnd || bnd_live(P, o, w, e));
+  // a block outside every boundary layer has nothing to compute or store
+  if (P.bnd && !__syncthreads_or(live)) return;
 
   double acc[NOUT][N1];
 #pragma unroll
   for (int j = 0; j < NOUT; ++j)
 #pragma unroll
     for (int q = 0; q < N1; ++q) acc[j][q] = 0.0;
-  if (valid) {
+  if (live) {
     for (int t = 0; t < P.nterm; ++t) {
       double u[N1], y[N1];
       load_elem<NORD, NC>(P.in[P.t_src[t]], line, P.inner, e, P.M, P.gofs, u);
@@ -216,7 +251,7 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
 
   double dotacc[kApplyMaxOut] = {0.0, 0.0, 0.0, 0.0};
   double rr = 0.0, bb = 0.0;
-  if (valid) {
+  if (live) {
     const bool has_node = e < K - 1;
     if (has_node) {
       if (te + 1 < TE) {
@@ -376,6 +411,45 @@ __device__ void stage_input_df(const double* x, bool is_df, long long plane, lon
   }
 }
 
+// Lines mode (contiguous axis, several lines per block): column c of the
+// tile is line w0 + c, rows g0 .. g0 + rows - 1 of it, stored [column][rows];
+// consecutive threads load consecutive rows of one line.
+template <bool NC>
+__device__ void stage_lines_df(const double* x, bool is_df, long long plane, long long w0, int M, int g0, int rows,
+                               int TW, int wvalid, float2* tile) {
+  const int total = rows * TW;
+  for (int i0 = threadIdx.x; i0 < total; i0 += kStageBatch * blockDim.x) {
+    uint2 v[kStageBatch];
+#pragma unroll
+    for (int k = 0; k < kStageBatch; ++k) {
+      const int i = i0 + k * blockDim.x;
+      const int c = i / rows, r = i - c * rows;
+      const int g = g0 + r;
+      v[k] = make_uint2(0u, 0u);
+      if (i < total && c < wvalid && g >= 0 && g < M) {
+        const long long off = (w0 + c) * (long long)M + g;
+        if (is_df) {
+          const float* f = reinterpret_cast<const float*>(x);
+          v[k] = make_uint2(__float_as_uint(ld_f32<NC>(f + off)), __float_as_uint(ld_f32<NC>(f + plane + off)));
+        } else {
+          const unsigned long long bits = (unsigned long long)__double_as_longlong(ld_f64<NC>(x + off));
+          v[k] = make_uint2((unsigned)bits, (unsigned)(bits >> 32));
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kStageBatch; ++k) {
+      const int i = i0 + k * blockDim.x;
+      if (i < total) {
+        df d;
+        if (is_df) d = {__uint_as_float(v[k].x), __uint_as_float(v[k].y)};
+        else d = split_f64(__longlong_as_double((long long)(((unsigned long long)v[k].y << 32) | v[k].x)));
+        tile[i] = make_float2(d.hi, d.lo);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ df slot_df(float2 v) { return {v.x, v.y}; }
 
 // y = E u for one element (all n+1 rows, or only row 0 when ROW0_ONLY) in
@@ -444,30 +518,43 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
   constexpr int N1 = C::N1;
   const int K = P.K;
   const int TE = NTHREADS / TW;
-  const long long wtiles = (P.inner + TW - 1) / TW;
+  // Lines mode: on the contiguous axis (inner == 1) the host may put TW > 1
+  // lines of TE elements into a block (TE about K), so that short lines do
+  // not leave most threads without an element; threads then run along the
+  // elements of a line and the tiles hold one column per line.
+  const bool lines = P.inner == 1 && TW > 1;
+  const long long npos = lines ? P.outer : P.inner;
+  const long long wtiles = (npos + TW - 1) / TW;
   const long long etiles = (K + TE - 1) / TE;
   const long long et = bx % etiles;
   bx /= etiles;
   const long long wt = bx % wtiles;
-  const long long o = bx / wtiles;
-  const int tw = threadIdx.x % TW, te = threadIdx.x / TW;
+  const long long o = lines ? 0 : bx / wtiles;
+  const int tw = lines ? (int)threadIdx.x / TE : (int)threadIdx.x % TW;
+  const int te = lines ? (int)threadIdx.x % TE : (int)threadIdx.x / TW;
+  const int estep = lines ? 1 : TW;   // thread-index distance to the next element of the same position
   const long long w0 = wt * TW;
   const long long w = w0 + tw;
   const int e = (int)(et * TE + te);
-  const bool valid = w < P.inner && e < K;
-  const long long line = o * (long long)P.M * P.inner + (valid ? w : 0);
+  const bool valid = w < npos && e < K;
+  const long long line = lines ? (valid ? w : 0) * (long long)P.M : o * (long long)P.M * P.inner + (valid ? w : 0);
   const long long plane = P.plane;
   const int rows = apply_df_rows(NORD, TE);
   const int g0 = NORD * (int)(et * TE) - 1;
-  const int wvalid = (int)min((long long)TW, P.inner - w0);
+  const int wvalid = (int)min((long long)TW, npos - w0);
+  const int rstride = lines ? 1 : TW;      // tile distance between rows of one column
+  const int cstride = lines ? rows : 1;    // and between columns
   // stage every input the block uses
   float2* tin[kApplyMaxIn];
   int nstaged = 0;
   for (int i = 0; i < kApplyMaxIn; ++i) {
     tin[i] = tiles + (size_t)nstaged * rows * TW;
     if (P.in[i]) {
-      stage_input_df<NC>(P.in[i], P.in_df[i] != 0, plane, o * (long long)P.M * P.inner + w0, P.inner, g0, rows, TW,
-                         wvalid, P.M, tin[i]);
+      if (lines)
+        stage_lines_df<NC>(P.in[i], P.in_df[i] != 0, plane, w0, P.M, g0, rows, TW, wvalid, tin[i]);
+      else
+        stage_input_df<NC>(P.in[i], P.in_df[i] != 0, plane, o * (long long)P.M * P.inner + w0, P.inner, g0, rows,
+                           TW, wvalid, P.M, tin[i]);
       ++nstaged;
     }
   }
@@ -479,8 +566,8 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
 #pragma unroll
   for (int j = 0; j < NOUT; ++j) {
     if (valid && j < P.nterm) {
-      elem_product_df<NORD, false>(S.es[j], S.ea[j], S.e1[j], S.has1[j], tin[P.t_src[j]] + NORD * te * TW + tw, TW,
-                                   acc[j]);
+      elem_product_df<NORD, false>(S.es[j], S.ea[j], S.e1[j], S.has1[j],
+                                   tin[P.t_src[j]] + NORD * te * rstride + tw * cstride, rstride, acc[j]);
     } else {
 #pragma unroll
       for (int q = 0; q < N1; ++q) acc[j][q] = df{0.0f, 0.0f};
@@ -496,14 +583,14 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
     if (has_node) {
       if (te + 1 < TE) {
 #pragma unroll
-        for (int j = 0; j < NOUT; ++j) acc[j][NORD] = df_add(acc[j][NORD], S.row0[j][threadIdx.x + TW]);
+        for (int j = 0; j < NOUT; ++j) acc[j][NORD] = df_add(acc[j][NORD], S.row0[j][threadIdx.x + estep]);
       } else {
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) {
           if (j < P.nterm) {
             df y[N1];
             elem_product_df<NORD, true>(S.es[j], S.ea[j], S.e1[j], S.has1[j],
-                                        tin[P.t_src[j]] + NORD * (te + 1) * TW + tw, TW, y);
+                                        tin[P.t_src[j]] + NORD * (te + 1) * rstride + tw * cstride, rstride, y);
             acc[j][NORD] = df_add(acc[j][NORD], y[0]);
           }
         }
@@ -526,7 +613,8 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
 #pragma unroll
         for (int j = 0; j < NOUT; ++j)
           if (j < P.nout)
-            tiles[((size_t)j * orows + NORD * te + r) * TW + tw] = make_float2(acc[j][r + 1].hi, acc[j][r + 1].lo);
+            tiles[(size_t)j * orows * TW + (size_t)(NORD * te + r) * rstride + (size_t)tw * (lines ? orows : 1)] =
+                make_float2(acc[j][r + 1].hi, acc[j][r + 1].lo);
       }
     }
     __syncthreads();
@@ -534,18 +622,25 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
     const int rows_out = min(orows, P.M - g_first);
     const int tw_shift = __ffs(TW) - 1;
     const long long base_off = o * (long long)P.M * P.inner + (long long)g_first * P.inner + w0;
-    for (int i = threadIdx.x; i < rows_out * TW; i += blockDim.x) {
-      const int rho = i >> tw_shift, c = i & (TW - 1);
-      if (c < wvalid) {
-        const long long off = base_off + (long long)rho * P.inner + c;
+    auto put = [&](int i, long long off) {
 #pragma unroll
-        for (int j = 0; j < NOUT; ++j)
-          if (j < P.nout) {
-            const float2 v = tiles[(size_t)j * orows * TW + i];
-            float* f = reinterpret_cast<float*>(P.out[j]);
-            f[off] = v.x;
-            f[plane + off] = v.y;
-          }
+      for (int j = 0; j < NOUT; ++j)
+        if (j < P.nout) {
+          const float2 v = tiles[(size_t)j * orows * TW + i];
+          float* f = reinterpret_cast<float*>(P.out[j]);
+          f[off] = v.x;
+          f[plane + off] = v.y;
+        }
+    };
+    if (lines) {   // tile index i = c * orows + rho
+      for (int i = threadIdx.x; i < orows * TW; i += blockDim.x) {
+        const int c = i / orows, rho = i - c * orows;
+        if (c < wvalid && rho < rows_out) put(i, (w0 + c) * (long long)P.M + g_first + rho);
+      }
+    } else {       // tile index i = rho * TW + c
+      for (int i = threadIdx.x; i < rows_out * TW; i += blockDim.x) {
+        const int rho = i >> tw_shift, c = i & (TW - 1);
+        if (c < wvalid) put(i, base_off + (long long)rho * P.inner + c);
       }
     }
     return;

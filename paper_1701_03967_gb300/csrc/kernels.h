@@ -55,7 +55,38 @@ struct ApplyParams {
   // 0: extent M, boundary values zero.  (outer / inner count the stored
   // positions of the other axes either way.)
   int gofs;
+  // with gofs: outputs are known to vanish outside the boundary layers (one
+  // element deep at each end of every axis), and the output fields start at
+  // zero; a thread whose element and position lie outside them skips its
+  // loads, products and stores.  bnd_M: interior extents of all axes.
+  int bnd, bnd_N, bnd_axis;
+  long long bnd_M[kMaxN];
 };
+
+// Tile width TW of the double-float apply (a block covers TW positions times
+// nthreads / TW elements): up to 32 consecutive positions of the axes after
+// the operated one; on the contiguous axis itself (inner == 1) TW lines of
+// about K elements each (K rounded up to a power of two, at least 8), no
+// more lines than there are -- TW > 1 with inner == 1 is the lines mode.
+inline int apply_df_tw(long long inner, long long outer, int K, int nthreads) {
+  int TW = 1;
+  if (inner > 1) {
+    while (TW * 2 <= 32 && TW * 2 <= inner) TW *= 2;
+    return TW;
+  }
+  int TE = 8;
+  while (TE < K && TE < nthreads) TE *= 2;
+  TW = nthreads / TE;
+  while (TW > 1 && TW / 2 >= outer) TW /= 2;
+  return TW;
+}
+// blocks of a double-float apply launch with tile width TW
+inline long long apply_df_blocks(long long inner, long long outer, int K, int TW, int nthreads) {
+  const bool lines = inner == 1 && TW > 1;
+  const long long npos = lines ? outer : inner;
+  const int TE = nthreads / TW;
+  return (lines ? 1 : outer) * ((npos + TW - 1) / TW) * ((K + TE - 1) / TE);
+}
 
 // The double-float apply handles one or two outputs, term t writing output t;
 // an addend, a residual base or a float32 output only with one output.
