@@ -39,23 +39,19 @@ int launch_apply_df(const ApplyParams& P, int TW, long long blocks, size_t smem,
 
 int launch_apply(const ApplyParams& P, cudaStream_t s) {
   if (P.outer * (long long)P.K * P.inner <= 0) return 0;
-  int TW = 1;
-  while (TW * 2 <= 32 && TW * 2 <= P.inner) TW *= 2;
-  const int TE = kApplyThreads / TW;
-  const long long blocks = P.outer * ((P.inner + TW - 1) / TW) * ((P.K + TE - 1) / TE);
+  const int TW = apply_tile_w(P.inner, P.outer, P.K, kApplyThreads);
+  const long long blocks = apply_tile_blocks(P.inner, P.outer, P.K, TW, kApplyThreads);
   if (P.df) {
     if (!apply_df_form_ok(P)) return (int)cudaErrorInvalidValue;
     int nin = 0;
     for (int i = 0; i < kApplyMaxIn; ++i) nin += P.in[i] != nullptr;
-    const int TWd = apply_df_tw(P.inner, P.outer, P.K, kApplyThreads);
-    const long long bdf = apply_df_blocks(P.inner, P.outer, P.K, TWd, kApplyThreads);
-    const size_t smem = apply_df_tile_bytes(P.n, TWd, kApplyThreads, nin);
+    const size_t smem = apply_df_tile_bytes(P.n, TW, kApplyThreads, nin);
     int rc = 0;
     switch (P.n) {
 #define FEMFFT_APPLY_DF_CASE(NN)                                                       \
   case NN:                                                                             \
-    rc = P.nout <= 1 ? launch_apply_df<NN, 1>(P, TWd, bdf, smem, s)                    \
-                     : launch_apply_df<NN, 2>(P, TWd, bdf, smem, s);                   \
+    rc = P.nout <= 1 ? launch_apply_df<NN, 1>(P, TW, blocks, smem, s)                  \
+                     : launch_apply_df<NN, 2>(P, TW, blocks, smem, s);                 \
     if (rc) return rc;                                                                 \
     break;
       FEMFFT_APPLY_DF_CASE(1) FEMFFT_APPLY_DF_CASE(2) FEMFFT_APPLY_DF_CASE(3) FEMFFT_APPLY_DF_CASE(4)

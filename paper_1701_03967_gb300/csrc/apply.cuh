@@ -212,18 +212,26 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
   constexpr int N1 = C::N1;
   const int K = P.K;
   const int TE = NTHREADS / TW;
-  const long long wtiles = (P.inner + TW - 1) / TW;
+  // lines mode (inner == 1, TW > 1): TW lines of the contiguous axis per
+  // block, threads along the elements of a line (as in apply_block_df)
+  const bool lines = P.inner == 1 && TW > 1;
+  const long long npos = lines ? P.outer : P.inner;
+  const long long wtiles = (npos + TW - 1) / TW;
   const long long etiles = (K + TE - 1) / TE;
   const long long et = bx % etiles;
   bx /= etiles;
   const long long wt = bx % wtiles;
-  const long long o = bx / wtiles;
-  const int tw = threadIdx.x % TW, te = threadIdx.x / TW;
+  const long long o = lines ? 0 : bx / wtiles;
+  const int tw = lines ? (int)threadIdx.x / TE : (int)threadIdx.x % TW;
+  const int te = lines ? (int)threadIdx.x % TE : (int)threadIdx.x / TW;
+  const int estep = lines ? 1 : TW;
   const long long w = wt * TW + tw;
   const int e = (int)(et * TE + te);
-  const bool valid = w < P.inner && e < K;
-  const long long line = o * (long long)(P.M + 2 * P.gofs) * P.inner + (valid ? w : 0);
-  const bool live = valid && (!P.bnd || bnd_live(P, o, w, e));
+  const bool valid = w < npos && e < K;
+  const long long Ms = P.M + 2 * P.gofs;   // stored extent of the operated axis
+  const long long line = lines ? (valid ? w : 0) * Ms : o * Ms * P.inner + (valid ? w : 0);
+  // in lines mode the line index is the outer index and no axis follows
+  const bool live = valid && (!P.bnd || (lines ? bnd_live(P, w, 0, e) : bnd_live(P, o, w, e)));
   // a block outside every boundary layer has nothing to compute or store
   if (P.bnd && !__syncthreads_or(live)) return;
 
@@ -256,7 +264,7 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
     if (has_node) {
       if (te + 1 < TE) {
 #pragma unroll
-        for (int j = 0; j < NOUT; ++j) acc[j][NORD] += S.row0[j][threadIdx.x + TW];
+        for (int j = 0; j < NOUT; ++j) acc[j][NORD] += S.row0[j][threadIdx.x + estep];
       } else {
         for (int t = 0; t < P.nterm; ++t) {
           double u[N1], y[N1];

@@ -668,16 +668,9 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
         st.ap = op.ap;
         st.mode = op.ap.nout;
         st.n = op.ap.n;
-        int TW = 1;
-        if (op.ap.df) {
-          TW = apply_df_tw(op.ap.inner, op.ap.outer, op.ap.K, kBatchThreads);
-        } else {
-          while (TW * 2 <= 32 && TW * 2 <= op.ap.inner) TW *= 2;
-        }
+        const int TW = apply_tile_w(op.ap.inner, op.ap.outer, op.ap.K, kBatchThreads);
         st.TW = TW;
-        st.units = op.ap.df ? apply_df_blocks(op.ap.inner, op.ap.outer, op.ap.K, TW, kBatchThreads)
-                            : op.ap.outer * ((op.ap.inner + TW - 1) / TW) * ((op.ap.K + kBatchThreads / TW - 1) /
-                                                                           (kBatchThreads / TW));
+        st.units = apply_tile_blocks(op.ap.inner, op.ap.outer, op.ap.K, TW, kBatchThreads);
         st.units_per_item = (int)std::max<long long>(1, kItemDof / ((long long)kBatchThreads * op.ap.n));
         if (op.ap.df) {
           int nin = 0;

@@ -63,12 +63,12 @@ struct ApplyParams {
   long long bnd_M[kMaxN];
 };
 
-// Tile width TW of the double-float apply (a block covers TW positions times
+// Tile width TW of the apply kernels (a block covers TW positions times
 // nthreads / TW elements): up to 32 consecutive positions of the axes after
 // the operated one; on the contiguous axis itself (inner == 1) TW lines of
 // about K elements each (K rounded up to a power of two, at least 8), no
 // more lines than there are -- TW > 1 with inner == 1 is the lines mode.
-inline int apply_df_tw(long long inner, long long outer, int K, int nthreads) {
+inline int apply_tile_w(long long inner, long long outer, int K, int nthreads) {
   int TW = 1;
   if (inner > 1) {
     while (TW * 2 <= 32 && TW * 2 <= inner) TW *= 2;
@@ -80,8 +80,8 @@ inline int apply_df_tw(long long inner, long long outer, int K, int nthreads) {
   while (TW > 1 && TW / 2 >= outer) TW /= 2;
   return TW;
 }
-// blocks of a double-float apply launch with tile width TW
-inline long long apply_df_blocks(long long inner, long long outer, int K, int TW, int nthreads) {
+// blocks of an apply launch with tile width TW
+inline long long apply_tile_blocks(long long inner, long long outer, int K, int TW, int nthreads) {
   const bool lines = inner == 1 && TW > 1;
   const long long npos = lines ? outer : inner;
   const int TE = nthreads / TW;
