@@ -15,26 +15,34 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_kernel(ApplyParams P, 
 // Four resident CTAs per SM (64 registers, small spills): the kernel waits on
 // latency, and 4 CTAs beat 2 (128 registers) and 3 (80) by 22 % and 7 %
 // (2D n = 9, K = 1024: 10.2 vs 12.9 and 10.9 ms per mixed step).
-template <int NORD, int NOUT>
+// LM: 1 for the lines mode of the contiguous axis, 0 otherwise (compiled
+// apart so that neither pays for the other's index selects: measured 2 % on
+// the 2D n = 9 headline apply)
+template <int NORD, int NOUT, int LM>
 __global__ void __launch_bounds__(kApplyThreads, 4) apply_kernel_df(ApplyParams P, int TW) {
   __shared__ ApplySmemDF<NORD, NOUT, kApplyThreads> S;
   extern __shared__ float2 tiles[];
   apply_stage_mats_df<NORD, NOUT, kApplyThreads>(P, S);
-  apply_block_df<NORD, NOUT, kApplyThreads, true>(P, TW, blockIdx.x, S, tiles);
+  apply_block_df<NORD, NOUT, kApplyThreads, true, LM>(P, TW, blockIdx.x, S, tiles);
 }
 
 // dynamic shared memory of a double-float launch, enabling it once per kernel
-template <int NORD, int NOUT>
-int launch_apply_df(const ApplyParams& P, int TW, long long blocks, size_t smem, cudaStream_t s) {
+template <int NORD, int NOUT, int LM>
+int launch_apply_df_lm(const ApplyParams& P, int TW, long long blocks, size_t smem, cudaStream_t s) {
   static size_t enabled = 48 * 1024;
   if (smem > enabled) {
-    cudaError_t e = cudaFuncSetAttribute(apply_kernel_df<NORD, NOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel_df<NORD, NOUT, LM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     enabled = smem;
   }
-  apply_kernel_df<NORD, NOUT><<<(unsigned)blocks, kApplyThreads, smem, s>>>(P, TW);
+  apply_kernel_df<NORD, NOUT, LM><<<(unsigned)blocks, kApplyThreads, smem, s>>>(P, TW);
   return 0;
+}
+template <int NORD, int NOUT>
+int launch_apply_df(const ApplyParams& P, int TW, long long blocks, size_t smem, cudaStream_t s) {
+  if (P.inner == 1 && TW > 1) return launch_apply_df_lm<NORD, NOUT, 1>(P, TW, blocks, smem, s);
+  return launch_apply_df_lm<NORD, NOUT, 0>(P, TW, blocks, smem, s);
 }
 
 int launch_apply(const ApplyParams& P, cudaStream_t s) {

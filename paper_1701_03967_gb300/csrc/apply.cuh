@@ -519,7 +519,9 @@ __device__ __forceinline__ void elem_product_df(const df* Es, const df* Ea, cons
 
 // Block bx of a double-float apply launch (same tiling as apply_block);
 // tiles: shared memory for the staged inputs (apply_df_tile_bytes).
-template <int NORD, int NOUT, int NTHREADS, bool NC>
+// LM: 0 the positions of the other axes per block, 1 lines mode (the caller
+// has checked inner == 1 and TW > 1), 2 decided here (the batched kernel)
+template <int NORD, int NOUT, int NTHREADS, bool NC, int LM = 2>
 __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, long long bx,
                                                ApplySmemDF<NORD, NOUT, NTHREADS>& S, float2* tiles) {
   using C = EO<NORD>;
@@ -530,7 +532,7 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
   // lines of TE elements into a block (TE about K), so that short lines do
   // not leave most threads without an element; threads then run along the
   // elements of a line and the tiles hold one column per line.
-  const bool lines = P.inner == 1 && TW > 1;
+  const bool lines = LM == 2 ? (P.inner == 1 && TW > 1) : LM == 1;
   const long long npos = lines ? P.outer : P.inner;
   const long long wtiles = (npos + TW - 1) / TW;
   const long long etiles = (K + TE - 1) / TE;
