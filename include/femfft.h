@@ -373,6 +373,16 @@ int fem_fft_batch_hold_step(fem_fft_batch batch, int64_t step);
  */
 int fem_fft_batch_order(int nprob, const int* nsteps, const double* work, int* h_prob, int* h_step);
 
+/*
+ * fem_fft_apply_tiling -- the block tiling of the operator apply launches
+ * (host only; no paper counterpart): for an axis of K elements with `outer`
+ * positions before it and `inner` after it (inner == 1: the contiguous axis),
+ * *h_tw positions per block (lines of the contiguous axis when inner == 1
+ * and *h_tw > 1, each with 256 / *h_tw element slots) and *h_blocks blocks.
+ * Either pointer may be NULL.  FEM_FFT_ERR_ARG for a non-positive size.
+ */
+int fem_fft_apply_tiling(int64_t inner, int64_t outer, int64_t K, int* h_tw, int64_t* h_blocks);
+
 /* Static text for a status code; fem_fft_last_error: the last CUDA error
  * text recorded by this thread (empty if none). */
 const char* fem_fft_strerror(int code);

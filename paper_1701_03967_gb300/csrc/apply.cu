@@ -1,5 +1,6 @@
 // Stand-alone operator-apply kernel (one launch per 1D application); the
 // device code is in apply.cuh.
+#include "../../include/femfft.h"
 #include "apply.cuh"
 
 namespace femfft {
@@ -87,3 +88,11 @@ int launch_apply(const ApplyParams& P, cudaStream_t s) {
 }
 
 }  // namespace femfft
+
+extern "C" int fem_fft_apply_tiling(int64_t inner, int64_t outer, int64_t K, int* h_tw, int64_t* h_blocks) {
+  if (inner < 1 || outer < 1 || K < 1 || K > (int64_t(1) << 30)) return FEM_FFT_ERR_ARG;
+  const int TW = femfft::apply_tile_w(inner, outer, (int)K, femfft::kApplyThreads);
+  if (h_tw) *h_tw = TW;
+  if (h_blocks) *h_blocks = femfft::apply_tile_blocks(inner, outer, (int)K, TW, femfft::kApplyThreads);
+  return FEM_FFT_OK;
+}
