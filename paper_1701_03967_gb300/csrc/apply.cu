@@ -14,8 +14,8 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_kernel(ApplyParams P, 
 }
 
 // Four resident CTAs per SM (64 registers, small spills): the kernel waits on
-// latency, and 4 CTAs beat 2 (128 registers) and 3 (80) by 22 % and 7 %
-// (2D n = 9, K = 1024: 10.2 vs 12.9 and 10.9 ms per mixed step).
+// latency, and 4 CTAs beat 2 (128 registers) and 3 (80) by 22 % and 7 % when
+// the occupancy was chosen (2D n = 9, K = 1024 mixed step).
 // LM: 1 for the lines mode of the contiguous axis, 0 otherwise (compiled
 // apart so that neither pays for the other's index selects: measured 2 % on
 // the 2D n = 9 headline apply)
