@@ -268,19 +268,25 @@ int fem_fft_profile_read(fem_fft_plan plan, int kind, int64_t* launches, double*
 /*
  * fem_fft_apply_noalloc -- d_b = L d_u (float64, matrix-free, the same
  * operator as fem_fft_apply) for callers that cannot allocate device memory at
- * the point of the call: it needs no plan and calls no cudaMalloc/cudaFree
- * (for example inside CUDA graph capture, in allocator hooks, or under a
- * framework that forbids allocation after warm-up).  The paper has no
- * counterpart; this is a service entry point of the library.
- *   N, n, h_K, h_X, h_a, c  as for fem_fft_plan_create
- *   d_u, d_b  caller-owned device arrays [nrhs][M_1..M_N], d_u != d_b
+ * the point of the call: it needs no plan and calls no cudaMalloc/cudaFree or
+ * allocating library routine (for example a host callback or allocator hook
+ * that must not re-enter the allocator, or a framework that forbids device
+ * allocation after its warm-up).  The paper has no counterpart; this is a
+ * service entry point of the library.
+ *   N, n, h_K, h_X, h_a, c  as for fem_fft_plan_create, with the same
+ *             validity rules (FEM_FFT_ERR_ARG otherwise)
+ *   d_u, d_b  caller-owned device arrays [nrhs][M_1..M_N]; the two ranges
+ *             must not overlap (FEM_FFT_ERR_ARG)
  * The float64 temporaries live in one static device array of 64 MiB that
  * every GPU loading this library holds until the process exits; a problem
- * needing more than 8 * DOF * T bytes (T = 0, 3, 4 temporaries for N = 1, 2,
- * 3) returns FEM_FFT_ERR_ARG before any launch.  All calls share that array:
+ * needing more than 8 * DOF * T bytes (T = 3, 4 temporaries for N = 2, 3;
+ * N = 1 needs none and is limited to 9 * 2^20 unknowns) returns
+ * FEM_FFT_ERR_ARG before any launch.  All calls share that array and it keeps
+ * the last call's contents (every temporary is written before it is read):
  * calls whose kernels overlap on the GPU race and must be serialised.  The
- * first call on a device looks up the array's address (cudaGetSymbolAddress)
- * and must come before any stream capture.  Asynchronous on stream.
+ * first call on a device looks up the array's address (cudaGetSymbolAddress,
+ * with that device current) and caches it; make that first call before any
+ * stream capture.  Asynchronous on stream.
  */
 int fem_fft_apply_noalloc(int N, int n, const int64_t* h_K, const double* h_X, const double* h_a, double c,
                           const double* d_u, double* d_b, int64_t nrhs, void* stream);

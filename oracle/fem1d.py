@@ -386,17 +386,6 @@ def _theorem1_vector(n, K, k, p):
     return s
 
 
-def theorem1_eigvec(n, K, k, lam):
-    """s_k^(l) for a given eigenvalue lam (float64), with p solving
-    G~(lam) p = -g(lam) (Section 3, Theorem 1, item 3)."""
-    bA, bC = element_blocks(n)
-    if n > 1:
-        p = -np.linalg.solve(bA["bt"] - lam * bC["bt"], bA["b"] - lam * bC["b"])
-    else:
-        p = np.zeros(0)
-    return _theorem1_vector(n, K, k, p)
-
-
 def theorem1_bubble(n, K, e_vec):
     """Eigenvector s_0^(l) of Section 3, Theorem 1, item 2: zero node values
     and interiors (-P)^{j-1} e^(l)."""

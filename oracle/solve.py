@@ -38,19 +38,12 @@ class Problem:
         self.M = tuple(fem1d.dof_count(self.n, k) for k in self.K)
         self.h = tuple(x / k for x, k in zip(self.X, self.K))
         self.s = tuple(4.0 / (h * h) for h in self.h)       # 4 h_i^-2
-        self._eig = {}
         self._ops = {}
         self._basis = {}
 
     @property
     def dof(self):
         return int(np.prod(self.M))
-
-    def eig1d(self, i):
-        key = (self.n, self.K[i])
-        if key not in self._eig:
-            self._eig[key] = fem1d.eig(self.n, self.K[i])
-        return self._eig[key]
 
     def basis1d(self, i):
         """(lam, S, cnorm2) of ``fem1d.theorem1_basis`` for axis i (cached per

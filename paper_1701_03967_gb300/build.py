@@ -43,18 +43,26 @@ def build(verbose=False, force=False):
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest_dep:
         return LIB
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(os.path.dirname(HERE), "include")]
+    newest_header = max(os.path.getmtime(f) for f in headers)
     jobs = []
     objs = []
+
+    def stale(src, obj):
+        # an object is rebuilt when its source or any header is newer
+        return force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), newest_header)
+
     for f in CU_SOURCES:
-        obj = os.path.join(BUILD, f + ".o")
+        src, obj = os.path.join(CSRC, f), os.path.join(BUILD, f + ".o")
         objs.append(obj)
-        jobs.append([nvcc] + ARCH + common + ["-lineinfo", "-Xptxas", "-v", "-c", os.path.join(CSRC, f), "-o", obj])
+        if stale(src, obj):
+            jobs.append([nvcc] + ARCH + common + ["-lineinfo", "-Xptxas", "-v", "-c", src, "-o", obj])
     for f in CPP_SOURCES:
-        obj = os.path.join(BUILD, f + ".o")
+        src, obj = os.path.join(CSRC, f), os.path.join(BUILD, f + ".o")
         objs.append(obj)
         # the double-double precompute needs IEEE operations without contraction
-        jobs.append([nvcc] + common + ["-Xcompiler", "-ffp-contract=off", "-c", os.path.join(CSRC, f), "-o", obj])
-    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+        if stale(src, obj):
+            jobs.append([nvcc] + common + ["-Xcompiler", "-ffp-contract=off", "-c", src, "-o", obj])
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         outs = list(ex.map(_run, jobs))
     if verbose:
         for o in outs:

@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -37,6 +39,22 @@ bool valid_K(int64_t K) {
 namespace femfft {
 
 void set_last_error(const std::string& what) { g_last_error = what; }
+
+int ensure_dyn_smem(const void* kernel, size_t smem) {
+  if (smem <= 48 * 1024) return (int)cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return (int)e;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> enabled;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = enabled[std::make_pair(kernel, dev)];
+  if (smem <= have) return (int)cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  have = smem;
+  return (int)cudaSuccess;
+}
 
 int cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);

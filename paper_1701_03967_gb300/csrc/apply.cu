@@ -30,13 +30,8 @@ __global__ void __launch_bounds__(kApplyThreads, 4) apply_kernel_df(ApplyParams 
 // dynamic shared memory of a double-float launch, enabling it once per kernel
 template <int NORD, int NOUT, int LM>
 int launch_apply_df_lm(const ApplyParams& P, int TW, long long blocks, size_t smem, cudaStream_t s) {
-  static size_t enabled = 48 * 1024;
-  if (smem > enabled) {
-    cudaError_t e = cudaFuncSetAttribute(apply_kernel_df<NORD, NOUT, LM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    enabled = smem;
-  }
+  const int e = ensure_dyn_smem((const void*)apply_kernel_df<NORD, NOUT, LM>, smem);
+  if (e) return e;
   apply_kernel_df<NORD, NOUT, LM><<<(unsigned)blocks, kApplyThreads, smem, s>>>(P, TW);
   return 0;
 }

@@ -93,14 +93,8 @@ size_t smem_budget(int n) {
 // The attribute only grows, so that graphs built for larger tiles stay
 // launchable after a later batch or tuning run.
 int enable_smem(int n, size_t smem) {
-  static size_t enabled[64][kMaxOrder + 1] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const int slot = dev >= 0 && dev < 64 ? dev : 0;
-  if (smem <= enabled[slot][n]) return FEM_FFT_OK;
-  cudaError_t e = cudaFuncSetAttribute(kernel_for(n), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail(e, "batch kernel shared memory");
-  enabled[slot][n] = smem;
+  const int e = ensure_dyn_smem(kernel_for(n), smem);
+  if (e) return cuda_fail((cudaError_t)e, "batch kernel shared memory");
   return FEM_FFT_OK;
 }
 

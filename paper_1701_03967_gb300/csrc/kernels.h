@@ -8,6 +8,12 @@ namespace femfft {
 
 struct PassParams;
 
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes on
+// the current device.  The limit is a per-device attribute: the largest value
+// set is remembered per (kernel, device) under a lock, so that concurrent
+// first launches and several GPUs are handled.  Returns a cudaError_t value.
+int ensure_dyn_smem(const void* kernel, size_t smem);
+
 // pencil passes (pencil_f64.cu / pencil_f32.cu): mode 0 forward, 1 inverse,
 // 2 fused forward/divide/inverse.  Returns a cudaError_t value.
 int launch_pencil_f64(int mode, int n, const PassParams& P, size_t smem, int threads, cudaStream_t s);

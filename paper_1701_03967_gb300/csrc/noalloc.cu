@@ -2,10 +2,10 @@
 // device allocation.
 //
 // Who needs this: code that may not call cudaMalloc at the point where it
-// applies the operator -- for example a step that runs while a CUDA graph is
-// being captured (allocation is not a capturable operation), a host callback
-// or custom-allocator hook that must not re-enter the allocator, or a
-// framework that forbids allocation after its warm-up.  Such callers own the
+// applies the operator -- for example a host callback or custom-allocator
+// hook that must not re-enter the allocator, a framework that forbids device
+// allocation after its warm-up, or a process whose device memory is fully
+// reserved by another allocator.  Such callers own the
 // input and output buffers; the float64 temporaries of the axis-by-axis
 // evaluation live in the fixed array below instead of plan workspace.
 //
@@ -13,8 +13,10 @@
 //  * The array holds kNoallocScratchBytes (64 MiB) on every GPU that loads
 //    this library, for the life of the process.  A call needs
 //    8 * DOF * T bytes, with DOF the unknowns of one right-hand side and
-//    T = 0 (1D), 3 (2D) or 4 (3D) temporaries; larger problems are rejected
-//    with FEM_FFT_ERR_ARG before anything is launched.  Right-hand sides are
+//    T = 0 (1D), 3 (2D) or 4 (3D) temporaries; larger problems (and 1D
+//    problems above 9 * 2^20 unknowns) are rejected with FEM_FFT_ERR_ARG
+//    before anything is launched, as are arguments plan creation rejects and
+//    input and output ranges that overlap.  Right-hand sides are
 //    processed one after the other through the same temporaries.
 //  * All calls share the array and it keeps the contents of the last call.
 //    Every temporary is completely written before it is read, so nothing has
@@ -26,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -208,18 +211,35 @@ extern "C" int fem_fft_apply_noalloc(int N, int n, const int64_t* h_K, const dou
   o.N = N;
   o.n = n;
   o.c = c;
+  // The same validity rules as fem_fft_plan_create (L positive definite).
+  // The unknown count is bounded while it is formed, so that no product of
+  // the accepted extents can wrap around: a 1D problem has at most
+  // 9 * 2^20 - 1 unknowns, and with temporaries the scratch size bounds it.
+  const int ntmp = N == 1 ? 0 : (N == 2 ? 3 : 4);
+  const long long dof_max = ntmp ? (long long)(kNoallocScratchBytes / (8 * (size_t)ntmp)) : (long long)9 << 20;
   long long dof = 1;
+  double cmin = 0.0;
   for (int i = 0; i < N; ++i) {
-    if (!k_supported(h_K[i]) || !(h_X[i] > 0.0) || !std::isfinite(h_a[i])) return FEM_FFT_ERR_ARG;
+    if (!k_supported(h_K[i]) || !(h_X[i] > 0.0) || !std::isfinite(h_X[i]) || !(h_a[i] > 0.0) ||
+        !std::isfinite(h_a[i]))
+      return FEM_FFT_ERR_ARG;
     o.K[i] = (int)h_K[i];
     o.M[i] = (long long)n * h_K[i] - 1;
     o.sa[i] = h_a[i] * 4.0 * (double)h_K[i] * (double)h_K[i] / (h_X[i] * h_X[i]);
+    if (o.M[i] > dof_max / dof) return FEM_FFT_ERR_ARG;   // too large for the scratch
     dof *= o.M[i];
+    cmin -= M_PI * M_PI * h_a[i] / (h_X[i] * h_X[i]);
   }
-  const int ntmp = N == 1 ? 0 : (N == 2 ? 3 : 4);
-  if ((double)dof * 8.0 * ntmp > (double)kNoallocScratchBytes) return FEM_FFT_ERR_ARG;   // too large
+  if (!std::isfinite(c) || !(c > cmin)) return FEM_FFT_ERR_ARG;
+  if (nrhs > (long long)(INT64_MAX / 8) / dof) return FEM_FFT_ERR_ARG;
   if (nrhs == 0) return FEM_FFT_OK;
-  if (!d_u || !d_b || d_u == d_b) return FEM_FFT_ERR_ARG;
+  if (!d_u || !d_b) return FEM_FFT_ERR_ARG;
+  // input and output ranges must be disjoint (the kernels read u while b is written)
+  {
+    const uintptr_t u0 = (uintptr_t)d_u, b0 = (uintptr_t)d_b;
+    const uintptr_t len = (uintptr_t)(nrhs * dof) * sizeof(double);
+    if (u0 < b0 + len && b0 < u0 + len) return FEM_FFT_ERR_ARG;
+  }
   void* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc) return rc;

@@ -8,12 +8,8 @@ namespace femfft {
 template <typename T, int NORD, int MODE, int WM>
 static int launch_wm(const PassParams& P, size_t smem, int threads, cudaStream_t s) {
   auto kern = pencil_pass_kernel<T, NORD, MODE, WM>;
-  static size_t configured = 0;   // max dynamic smem already enabled for this instantiation
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    configured = smem;
-  }
+  const int e = ensure_dyn_smem((const void*)kern, smem);
+  if (e) return e;
   kern<<<(unsigned)P.g.tiles, threads, smem, s>>>(P);
   return (int)cudaGetLastError();
 }

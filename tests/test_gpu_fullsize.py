@@ -35,6 +35,7 @@ def test_fullsize_fp64_and_mixed_match_oracle(name, wl, cfg):
     b = synth.normal_field(prob.M, cfg, 0, 1 if len(wl["K"]) == 3 and wl["n"] == 4 else 0)
     want = osolve.solve(prob, b)
     nrm = np.linalg.norm(want)
+    wmax = np.max(np.abs(want))
     bt = torch.from_numpy(b).cuda()
     # both algorithms of Section 4 at the same bars
     for algo, precision, tol in (("a", "fp64", 1e-12), ("a", "mixed", 1e-10), ("b", "fp64", 1e-12),
@@ -44,8 +45,10 @@ def test_fullsize_fp64_and_mixed_match_oracle(name, wl, cfg):
         got = plan.solve(bt).cpu().numpy()
         plan.close()
         rel = float(np.linalg.norm(got - want) / nrm)
-        print(f"{name} algorithm ({algo}) {precision} rel err {rel:.3e}")
+        relmax = float(np.max(np.abs(got - want)) / wmax)
+        print(f"{name} algorithm ({algo}) {precision} rel err {rel:.3e} (max norm {relmax:.3e})")
         assert rel <= tol, (name, algo, precision, rel)
+        assert relmax <= tol, (name, algo, precision, relmax)
         del got
     torch.cuda.empty_cache()
 
@@ -86,8 +89,10 @@ def test_fullsize_dirichlet_data_reproduce_a_polynomial(precision, tol):
     got = plan.solve_dirichlet(torch.from_numpy(b).cuda(), torch.from_numpy(g).cuda()).cpu().numpy()
     plan.close()
     rel = float(np.linalg.norm(got - want) / np.linalg.norm(want))
-    print(f"dirichlet 2d_n9_K1024 {precision} rel err {rel:.3e}")
+    relmax = float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+    print(f"dirichlet 2d_n9_K1024 {precision} rel err {rel:.3e} (max norm {relmax:.3e})")
     assert rel <= tol
+    assert relmax <= tol
     torch.cuda.empty_cache()
 
 
@@ -110,12 +115,15 @@ def test_fullsize_smooth_right_hand_side(name, wl, cfg):
     b = np.ascontiguousarray(scale * b)
     want = osolve.solve(prob, b)
     nrm = np.linalg.norm(want)
+    wmax = np.max(np.abs(want))
     bt = torch.from_numpy(b).cuda()
     for precision, tol in (("fp64", 1e-12), ("mixed", 1e-10)):
         plan = Plan(wl["n"], wl["K"], wl["X"], wl["a"], wl["c"], precision=precision)
         got = plan.solve(bt).cpu().numpy()
         plan.close()
         rel = float(np.linalg.norm(got - want) / nrm)
-        print(f"{name} smooth {precision} rel err {rel:.3e}")
+        relmax = float(np.max(np.abs(got - want)) / wmax)
+        print(f"{name} smooth {precision} rel err {rel:.3e} (max norm {relmax:.3e})")
         assert rel <= tol, (name, precision, rel)
+        assert relmax <= tol, (name, precision, relmax)
     torch.cuda.empty_cache()

@@ -30,6 +30,12 @@ def _rel(x, y):
     return float(np.linalg.norm(x - y) / np.linalg.norm(y))
 
 
+def _relmax(x, y):
+    """Relative max-norm error: a localised error (one bad pencil or boundary
+    element) that a relative L2 norm over many unknowns would hide."""
+    return float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
+
+
 CASES = [
     dict(n=3, K=(8,), X=(1.3,), a=(0.7,), c=0.2),
     dict(n=9, K=(16,), c=1.0),
@@ -63,6 +69,7 @@ def test_solve_fp64_matches_oracle(case):
     plan = _plan(case, "fp64", max_nrhs=2)
     got = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
     assert _rel(got, want) <= 1e-12
+    assert _relmax(got, want) <= 1e-12
 
 
 @pytest.mark.parametrize("case", CASES, ids=_ids)
@@ -74,6 +81,7 @@ def test_solve_mixed_matches_oracle(case):
     plan.set_refinement(0.0, 2)
     got = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
     assert _rel(got, want) <= 1e-10
+    assert _relmax(got, want) <= 1e-10
 
 
 @pytest.mark.parametrize("case", CASES[::2], ids=_ids)
@@ -84,6 +92,7 @@ def test_apply_matches_oracle(case):
     plan = _plan(case, "fp64", max_nrhs=2)
     got = plan.apply(torch.from_numpy(u).cuda()).cpu().numpy()
     assert _rel(got, want) <= 1e-13
+    assert _relmax(got, want) <= 1e-13
 
 
 def _bubble_signs(plan, prob):
@@ -115,9 +124,11 @@ def test_forward_and_inverse_transforms_match_oracle(case):
         shape[i] = prob.M[i]
         S = S * s.reshape(shape)
     assert _rel(got * S, want) <= 1e-12
+    assert _relmax(got * S, want) <= 1e-12
     w = synth.normal_field(prob.M, synth.CFG_TEST, 105)
     got_w = plan.inverse(torch.from_numpy(w * S).cuda()).cpu().numpy()
     assert _rel(got_w, osolve.inverse_expansion(prob, w)) <= 1e-12
+    assert _relmax(got_w, osolve.inverse_expansion(prob, w)) <= 1e-12
 
 
 def test_manufactured_solution_error_matches_paper_table():
@@ -141,10 +152,12 @@ def test_edge_cases():
     b = synth.normal_batch(5, prob.M, synth.CFG_TEST, 106)
     got = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
     assert _rel(got, osolve.solve(prob, b)) <= 1e-12
+    assert _relmax(got, osolve.solve(prob, b)) <= 1e-12
     # in-place FP64 solve
     bt = torch.from_numpy(b[:2].copy()).cuda()
     plan.solve(bt, out=bt)
     assert _rel(bt.cpu().numpy(), osolve.solve(prob, b[:2])) <= 1e-12
+    assert _relmax(bt.cpu().numpy(), osolve.solve(prob, b[:2])) <= 1e-12
     # zero right-hand sides
     z = torch.zeros((0,) + prob.M, dtype=torch.float64, device="cuda")
     plan.solve(z)
@@ -177,6 +190,7 @@ def test_grad_coeffs_match_oracle(case):
     np.testing.assert_allclose(ga_g, ga, rtol=1e-10)
     np.testing.assert_allclose(gc_g, gc, rtol=1e-10)
     assert _rel(lam.cpu().numpy(), gf) <= 1e-12
+    assert _relmax(lam.cpu().numpy(), gf) <= 1e-12
 
 
 @pytest.mark.parametrize("case", [dict(n=9, K=(16, 32), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
@@ -195,7 +209,9 @@ def test_mixed_residual_precisions(case):
         plan.set_residual_precision(mode)
         out[mode] = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
         assert _rel(out[mode], want) <= 1e-10, (mode, _rel(out[mode], want))
+        assert _relmax(out[mode], want) <= 1e-10
     assert _rel(out["df64"], out["f64"]) <= 1e-11
+    assert _relmax(out["df64"], out["f64"]) <= 1e-11
 
 
 @pytest.mark.parametrize("case", [dict(n=3, K=(8, 12), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
@@ -213,11 +229,13 @@ def test_mass_apply_and_heat_steps(case, precision, tol):
                      max_nrhs=2)
     ut, bt = torch.from_numpy(u0).cuda(), torch.from_numpy(b).cuda()
     assert _rel(st.plan.apply_mass(ut).cpu().numpy(), osolve.mass_apply(prob, u0)) <= 1e-13
+    assert _relmax(st.plan.apply_mass(ut).cpu().numpy(), osolve.mass_apply(prob, u0)) <= 1e-13
     want = u0
     for _ in range(5):
         ut = st.step(ut, bt)
         want = osolve.heat_step(prob, want, b, tau)
     assert _rel(ut.cpu().numpy(), want) <= tol
+    assert _relmax(ut.cpu().numpy(), want) <= tol
     st.close()
 
 
@@ -233,6 +251,7 @@ def test_tuned_plan_matches_oracle(case, precision, tol):
     plan.tune()
     got = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
     assert _rel(got, osolve.solve(prob, b)) <= tol
+    assert _relmax(got, osolve.solve(prob, b)) <= tol
 
 
 ALGO_B_CASES = [dict(n=9, K=(16, 32), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
@@ -257,13 +276,16 @@ def test_algorithm_b_matches_oracle(case, precision, tol):
     plan.set_algorithm("b")
     got = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
     assert _rel(got, osolve.solve(prob, b)) <= tol
+    assert _relmax(got, osolve.solve(prob, b)) <= tol
     assert _rel(got, osolve.solve_b(prob, b)) <= max(tol, 1e-11)
+    assert _relmax(got, osolve.solve_b(prob, b)) <= max(tol, 1e-11)
     # new coefficients rebuild the band tables
     a2 = tuple(1.3 * x for x in (case.get("a") or (1.0,) * len(case["K"])))
     plan.set_coefficients(a2, 0.5)
     prob2 = osolve.Problem(case["n"], case["K"], case.get("X"), a2, 0.5)
     got2 = plan.solve(torch.from_numpy(b).cuda()).cpu().numpy()
     assert _rel(got2, osolve.solve(prob2, b)) <= tol
+    assert _relmax(got2, osolve.solve(prob2, b)) <= tol
 
 
 def test_algorithm_b_needs_two_axes():

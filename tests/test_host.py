@@ -67,3 +67,28 @@ def test_host_rejects_bad_sizes():
     for n, K in [(0, 8), (10, 8), (3, 5), (3, 1), (3, 10), (3, 7)]:
         rc, *_ = _precompute(n, K)
         assert rc == -1, (n, K)
+
+
+def test_noalloc_rejects_oversized_and_invalid_problems_without_a_device_call():
+    """fem_fft_apply_noalloc validates before any device call: 3D extents
+    whose unknown count would overflow a signed 64-bit product, problems
+    beyond its static scratch, and coefficients fem_fft_plan_create rejects
+    all return FEM_FFT_ERR_ARG (-1), here with nrhs = 0 and NULL buffers."""
+    L = _lib()
+    f = L.fem_fft_apply_noalloc
+
+    def call(N, n, K, X=None, a=None, c=0.0, nrhs=0):
+        Kc = (ctypes.c_int64 * N)(*K)
+        Xc = (ctypes.c_double * N)(*(X or [1.0] * N))
+        ac = (ctypes.c_double * N)(*(a or [1.0] * N))
+        return f(N, n, Kc, Xc, ac, c, None, None, nrhs, None)
+
+    # (3 * 708588 - 1)^3 wraps a signed 64-bit product
+    assert call(3, 3, (708588, 708588, 708588)) == -1
+    assert call(3, 9, (1 << 20, 1 << 20, 1 << 20)) == -1
+    assert call(2, 9, (1024, 1024)) == -1                  # 3 x 680 MB of temporaries
+    assert call(1, 9, (3 << 20,)) == -1                    # K beyond 2^20
+    assert call(2, 2, (16, 16), a=[1.0, 0.0]) == -1        # a_i must be positive
+    assert call(2, 2, (16, 16), c=-2.0 * np.pi ** 2) == -1  # L not positive definite
+    assert call(2, 2, (16, 15)) == -1                      # K must be 2^p 3^q, p >= 1
+    assert call(2, 2, (16, 16)) == 0                       # valid, nrhs = 0: a no-op

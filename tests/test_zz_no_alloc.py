@@ -1,8 +1,9 @@
 """The allocation-free operator apply (fem_fft_apply_noalloc), called through
 the C ABI, against the plan-based fem_fft_apply.
 
-Callers that cannot allocate device memory where they apply the operator
-(graph capture, allocator hooks, no-allocation frameworks) use the
+Callers that cannot allocate device memory where they apply the operator (a
+host callback or allocator hook that must not re-enter the allocator, a
+framework that forbids device allocation after its warm-up) use the
 allocation-free entry point; its temporaries live in a static device array
 shared by all calls.  This file is collected last so that a run stopping at
 the first failure has already run every other test; it also passes on its own
@@ -45,8 +46,17 @@ def test_noalloc_apply_matches_plan_apply_twice(case):
         u = torch.from_numpy(synth.normal_batch(2, plan.M, synth.CFG_TEST, 300 + call)).cuda()
         want = plan.apply(u)
         got = torch.full_like(u, float("nan"))
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
         assert _noalloc(L, case, u, got) == 0
         torch.cuda.synchronize()
+        # the call takes no memory from torch's allocator; after the first
+        # call (which may load the library's device module holding the static
+        # array) none from the driver either
+        assert torch.cuda.memory_allocated() == alloc0
+        if call > 0:
+            assert torch.cuda.mem_get_info()[0] == free0
         rel = float(torch.linalg.norm(got - want) / torch.linalg.norm(want))
         assert rel <= 1e-13, (call, rel)
     plan.close()
@@ -59,3 +69,17 @@ def test_noalloc_rejects_problems_beyond_the_scratch():
     small = torch.zeros((1, 4), dtype=torch.float64, device="cuda")
     # rejected by the size check before any launch: the buffers are never touched
     assert _noalloc(L, big, small, small.clone()) == -1
+
+
+def test_noalloc_rejects_overlapping_ranges():
+    from paper_1701_03967_gb300 import _lib
+    L = _lib.lib()
+    case = CASES[1]
+    M = 1
+    for k in case["K"]:
+        M *= case["n"] * k - 1
+    buf = torch.zeros((3, M), dtype=torch.float64, device="cuda")
+    # b starts inside u's range (u = rows 0..1, b = rows 1..2): rejected before any launch
+    u = buf[0:2]
+    b = buf[1:3]
+    assert _noalloc(L, case, u, b) == -1
