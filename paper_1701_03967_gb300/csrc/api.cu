@@ -206,6 +206,12 @@ int upload_axis(fem_fft_plan p, const AxisHost& ax, DevTables* d, cudaStream_t s
   if ((rc = upload<T>(p, ax.fwd, &d->fwd, s))) return rc;
   if ((rc = upload<T>(p, ax.inv, &d->inv, s))) return rc;
   if ((rc = upload<T>(p, ax.mu, &d->mu, s))) return rc;
+  if (ax.fast_V) {
+    if ((rc = upload<T>(p, ax.tw2, &d->tw2, s))) return rc;
+    if ((rc = upload<T>(p, ax.gmap, &d->gmap, s))) return rc;
+    if ((rc = upload<T>(p, ax.invn, &d->invn, s))) return rc;
+    if ((rc = upload<T>(p, ax.muk, &d->muk, s))) return rc;
+  }
   return FEM_FFT_OK;
 }
 
@@ -305,11 +311,123 @@ int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inn
   return FEM_FFT_OK;
 }
 
+// Register-radix passes (pencil_fast.cuh): float32 plans, power-of-two K in
+// [16, 1024].  Pencils per tile W: as many as the shared memory holds (a
+// power of two for strided pencils), no more than keep about two tiles per
+// SM, at most what the sequence build covers (W K <= 8 threads); a tuned W
+// (fem_fft_plan_tune) replaces the heuristic.
+struct FastPlan {
+  FastParams P;
+  size_t smem;
+  int threads;
+};
+
+bool fast_eligible(fem_fft_plan p, int mode, int axis, bool f64) {
+  return p->fast_passes && !f64 && !p->rec && p->ax[axis].fast_V && p->t32[axis].gmap &&
+         (mode == MODE_FWD || mode == MODE_INV || mode == MODE_FUSED);
+}
+
+int plan_fast(fem_fft_plan p, int mode, int axis, long long outer, long long inner, int Wwant, FastPlan* fp) {
+  const AxisHost& ax = p->ax[axis];
+  const int n = p->n, K = ax.K, Q = n / 2 + 1, Qp = Q | 1;
+  const int threads = ax.fast_V == 32 ? fast_threads<32>() : fast_threads<16>();
+  FastParams& P = fp->P;
+  std::memset(&P, 0, sizeof(P));
+  const size_t csize = 2 * sizeof(float);
+  const size_t budget = (size_t)std::min(p->smem_optin, 220 * 1024);
+  long long wmax = (long long)(budget / ((size_t)(K * Qp + 16) * csize));
+  wmax = std::min<long long>(wmax, std::min<long long>(kMaxW, (long long)kFastChunkTasks * threads / K));
+  if (wmax < 1) return FEM_FFT_ERR_ARG;
+  long long W;
+  if (Wwant > 0) {
+    W = std::min<long long>(Wwant, wmax);
+  } else if (inner == 1) {
+    W = std::min<long long>(wmax, std::max<long long>(1, outer / (2 * 152)));
+  } else {
+    W = std::min<long long>(wmax, inner);
+    long long tiles = outer * ((inner + W - 1) / W);
+    while (W > 1 && tiles < 2 * 152) {
+      W /= 2;
+      tiles = outer * ((inner + W - 1) / W);
+    }
+  }
+  if (inner > 1) {
+    long long p2 = 1;
+    while (p2 * 2 <= W) p2 *= 2;
+    W = p2;
+  }
+  P.g.outer = outer;
+  P.g.inner = inner;
+  P.g.M = (int)ax.M;
+  P.g.W = (int)W;
+  if (inner == 1) {
+    P.g.tiles_inner = 1;
+    P.g.tiles = (outer + W - 1) / W;
+  } else {
+    P.g.tiles_inner = (inner + W - 1) / W;
+    P.g.tiles = outer * P.g.tiles_inner;
+  }
+  P.K = K;
+  P.Qp = Qp;
+  P.V = ax.fast_V;
+  P.Tn = K / ax.fast_V;
+  P.npass = ax.fast_npass;
+  for (int s = 0; s < kFastMaxPass; ++s) {
+    P.radix[s] = ax.fast_radix[s];
+    P.lprod[s] = ax.fast_lprod[s];
+    P.twofs[s] = ax.fast_twofs[s];
+  }
+  fast_layout(K, Q, Qp, (int)W, P.V, P.npass, P.radix, threads, &P.seq_order, &P.pitch, P.swz);
+  const DevTables& d = p->t32[axis];
+  P.tw2 = d.tw2;
+  P.rot = d.rot;
+  P.gmap = d.gmap;
+  P.invn = d.invn;
+  P.muk = d.muk;
+  (void)mode;
+  fp->smem = (size_t)W * P.pitch * csize;
+  fp->threads = threads;
+  return FEM_FFT_OK;
+}
+
+int run_fast(fem_fft_plan p, int mode, int axis, long long outer, long long inner, const void* in, bool in_f64,
+             void* out, bool out_f64, bool accum, cudaStream_t s) {
+  FastPlan fp;
+  int rc = plan_fast(p, mode, axis, outer, inner, p->fast_W[mode][axis], &fp);
+  if (rc) return rc;
+  FastParams& P = fp.P;
+  P.in = in;
+  P.out = out;
+  P.in_f64 = in_f64;
+  P.out_f64 = out_f64;
+  P.accum = accum;
+  if (mode == MODE_FUSED) {
+    P.dv.c = p->c;
+    P.dv.nother = p->N - 1;
+    for (int j = 1; j < p->N; ++j) {
+      P.dv.Mo[j - 1] = p->M[j];
+      P.dv.mu_o[j - 1] = p->t32[j].mu;
+    }
+  }
+  const double elems = (double)outer * P.g.M * inner;
+  const double bytes = elems * ((in_f64 ? 8 : 4) + (out_f64 ? 8 : 4) * (accum ? 2 : 1));
+  const int kind = mode == MODE_FWD ? 0 : (mode == MODE_FUSED ? 1 : 2);
+  int e;
+  {
+    ProfScope scope(p, s, kind, bytes, 0.0);
+    e = launch_fast_f32(mode, p->n, P, fp.smem, fp.threads, s);
+  }
+  if (e) return cuda_fail((cudaError_t)e, "pencil pass launch");
+  return FEM_FFT_OK;
+}
+
 int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const void* in, bool in_f64,
              void* out, bool out_f64, bool accum, cudaStream_t s) {
   long long outer = nrhs, inner = 1;
   for (int j = 0; j < axis; ++j) outer *= p->M[j];
   for (int j = axis + 1; j < p->N; ++j) inner *= p->M[j];
+  if (fast_eligible(p, mode, axis, f64))
+    return run_fast(p, mode, axis, outer, inner, in, in_f64, out, out_f64, accum, s);
   PassPlan pp;
   int rc = plan_pass(p, mode, axis, outer, inner, f64, &pp);
   if (rc) return rc;
@@ -1091,6 +1209,16 @@ int fem_fft_plan_set_coefficients(fem_fft_plan p, const double* h_a, double c, v
     AxisHost& ax = p->ax[i];
     ax.a = h_a[i];
     for (int m = 0; m < ax.M; ++m) ax.mu[m] = ax.a * ax.s * ax.lam[m];
+    fast_muk_update(&ax);
+    if (ax.fast_V) {
+      std::vector<float> k32(ax.muk.begin(), ax.muk.end());
+      if (p->t64[i].muk)
+        FEMFFT_CUDA(cudaMemcpyAsync(p->t64[i].muk, ax.muk.data(), ax.muk.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, s), "coefficients");
+      if (p->t32[i].muk)
+        FEMFFT_CUDA(cudaMemcpyAsync(p->t32[i].muk, k32.data(), k32.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+                    "coefficients");
+    }
     std::vector<float> f32(ax.mu.begin(), ax.mu.end());
     FEMFFT_CUDA(cudaMemcpyAsync(p->t64[i].mu, ax.mu.data(), ax.M * sizeof(double), cudaMemcpyHostToDevice, s),
                 "coefficients");
@@ -1300,6 +1428,37 @@ int fem_fft_plan_tune(fem_fft_plan p, void* stream) {
   passes.push_back({MODE_FUSED, 0});
   for (int ax = 1; ax < p->N; ++ax) passes.push_back({MODE_INV, ax});
   for (const Pass& ps : passes) {
+    if (fast_eligible(p, ps.mode, ps.axis, f64)) {
+      // register-radix pass: pencils per tile W in 1, 2, 4, ... (the radix
+      // schedule is fixed by K)
+      int bestW = 0;
+      float best_ms = 1e30f;
+      long long outer = p->max_nrhs, inner = 1;
+      for (int j = 0; j < ps.axis; ++j) outer *= p->M[j];
+      for (int j = ps.axis + 1; j < p->N; ++j) inner *= p->M[j];
+      for (int W = 1; W <= kMaxW && !rc; W *= 2) {
+        FastPlan fp;
+        if (plan_fast(p, ps.mode, ps.axis, outer, inner, W, &fp) || fp.P.g.W != W) continue;
+        p->fast_W[ps.mode][ps.axis] = W;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && !rc; ++rep) {
+          cudaEventRecord(e0, s);
+          rc = run_pass(p, ps.mode, ps.axis, p->max_nrhs, f64, buf, f64, buf, f64, false, s);
+          cudaEventRecord(e1, s);
+          if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = FEM_FFT_ERR_CUDA;
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          if (rep > 0) ms = std::min(ms, t);
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          bestW = W;
+        }
+      }
+      p->fast_W[ps.mode][ps.axis] = bestW;   // 0: the heuristic
+      if (rc) break;
+      continue;
+    }
     fem_fft_plan_s::Tuned& tu = p->tuned[ps.mode][ps.axis][f64 ? 1 : 0];
     const int K = (int)p->K[ps.axis];
     fem_fft_plan_s::Tuned best;

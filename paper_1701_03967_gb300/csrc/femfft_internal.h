@@ -7,6 +7,7 @@ namespace femfft {
 
 constexpr int kMaxN = 3;     // spatial dimensions
 constexpr int kMaxOrder = 9; // element order n
+constexpr int kFastMaxPass = 4;   // FFT passes of the register-radix pencil kernels
 
 // Host-side 1D tables of one axis (all float64, computed in double-double and
 // rounded once).  Spectral order of the M = nK-1 coefficients: sigma + 1 =
@@ -25,7 +26,24 @@ struct AxisHost {
   std::vector<double> inv;     // [K][2Q][n] per-k inverse maps; k = 0: bubble map
   std::vector<double> pvec;    // [K][n][n-1] p_k^(l) (k = 0: e^(l)), for tests
   std::vector<int> parity;     // [n-1] +1 even / -1 odd bubble eigenvector
+  // tables of the register-radix passes (pencil_fast.cuh), for power-of-two
+  // K in [16, 1024]; empty otherwise (fast_V == 0)
+  int fast_V = 0, fast_npass = 0;
+  int fast_radix[4] = {0, 0, 0, 0}, fast_lprod[4] = {0, 0, 0, 0}, fast_twofs[4] = {0, 0, 0, 0};
+  std::vector<double> tw2;     // four-step twiddles [R0][K/R0], (re, im) pairs: exp(-2 pi i r i / K)
+  std::vector<double> gmap;    // [2Q][n][K] inverse maps G_k[j][l] (the fwd table's transposed layout)
+  std::vector<double> invn;    // [n][K] 1 / ||s_k^(l)||_C^2 (k = 0: 1/K, bubble modes l < n-1)
+  std::vector<double> muk;     // [n][K] a s lambda of mode (k, l) (k = 0: bubble modes l < n-1)
 };
+
+// FFT schedule of the register-radix passes: V = 32 values per thread for
+// K >= 512, else 16; passes of radix min(V, remaining).  False when K is not a
+// power of two in [16, 1024].
+bool fast_schedule(int K, int* V, int* npass, int* radix);
+// Fill the fast_* tables of an axis whose base tables are computed (no-op
+// when K is not eligible); fast_muk_update recomputes muk after a change of a.
+void fast_tables(AxisHost* ax);
+void fast_muk_update(AxisHost* ax);
 
 // Precompute the tables of one axis.  Returns 0 or a negative status.
 int precompute_axis(int n, int K, double X, double a, AxisHost* out);

@@ -19,6 +19,18 @@ int ensure_dyn_smem(const void* kernel, size_t smem);
 int launch_pencil_f64(int mode, int n, const PassParams& P, size_t smem, int threads, cudaStream_t s);
 int launch_pencil_f32(int mode, int n, const PassParams& P, size_t smem, int threads, cudaStream_t s);
 
+// register-radix passes (pencil_fast_*.cu), float32, V = 16 or 32 values per
+// thread.  Returns a cudaError_t value.
+struct FastParams;
+int launch_fast_f32(int mode, int n, const FastParams& P, size_t smem, int threads, cudaStream_t s);
+
+// Shared-memory layout of a register-radix tile (a bank-conflict model of
+// the FFT exchanges and the map phase, evaluated on the host): the sequence
+// order, the pencil pitch (complex values) and the swizzle of each
+// intermediate buffer that minimise shared-memory wavefronts.
+void fast_layout(int K, int Q, int Qp, int W, int V, int npass, const int* radix, int nthreads, int* order,
+                 int* pitch, int* swz);
+
 // Matrix-free float64 application of element-block operators along one axis
 // (apply.cu).  Every term adds mats[t] (an (n+1)x(n+1) element matrix,
 // row-major) applied along the axis to input src[t] into output dst[t].

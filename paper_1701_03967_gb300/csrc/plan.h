@@ -10,6 +10,7 @@
 #include "femfft_internal.h"
 #include "kernels.h"
 #include "pencil.cuh"
+#include "pencil_fast.cuh"
 
 namespace femfft {
 
@@ -19,6 +20,11 @@ struct DevTables {
   void* fwd = nullptr;
   void* inv = nullptr;
   void* mu = nullptr;
+  // register-radix passes (pencil_fast.cuh); null when the axis is not eligible
+  void* tw2 = nullptr;
+  void* gmap = nullptr;
+  void* invn = nullptr;
+  void* muk = nullptr;
 };
 
 // One launch of a solve chain, recorded instead of launched: the batched
@@ -96,6 +102,10 @@ struct fem_fft_plan_s {
     int W = 0, V = 0;
   };
   Tuned tuned[3][femfft::kMaxN][2];
+  // float passes on the register-radix kernels where the axis allows it
+  // (fem_fft_set_pass_kernels); pencils per tile chosen by fem_fft_plan_tune
+  int fast_passes = 1;
+  int fast_W[3][femfft::kMaxN] = {{0}};
   // algorithm (b) of Section 4 (fem_fft_set_algorithm): band-solve tables
   // per position of the later axes (float64 and float32 copies), the element
   // data and the vertex-solve scratch

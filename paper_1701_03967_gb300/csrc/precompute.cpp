@@ -450,7 +450,69 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
     (void)theta;
   }
   for (int i = 0; i < M; ++i) ax.mu[i] = a * ax.s * ax.lam[i];
+  fast_tables(&ax);
   return 0;
+}
+
+bool fast_schedule(int K, int* V, int* npass, int* radix) {
+  if (K < 16 || K > 1024 || (K & (K - 1))) return false;
+  const int v = K >= 512 ? 32 : 16;
+  int np = 0, rem = K;
+  while (rem > 1) {
+    const int R = std::min(v, rem);
+    radix[np++] = R;
+    rem /= R;
+  }
+  *V = v;
+  *npass = np;
+  return true;
+}
+
+void fast_muk_update(AxisHost* axp) {
+  AxisHost& ax = *axp;
+  if (!ax.fast_V) return;
+  const int n = ax.n, K = ax.K;
+  ax.muk.assign((size_t)n * K, 0.0);
+  for (int l = 0; l + 1 < n; ++l) ax.muk[(size_t)l * K] = ax.mu[l];
+  for (int k = 1; k < K; ++k)
+    for (int l = 0; l < n; ++l) ax.muk[(size_t)l * K + k] = ax.mu[n * k - 1 + l];
+}
+
+void fast_tables(AxisHost* axp) {
+  AxisHost& ax = *axp;
+  ax.fast_V = 0;
+  int V, np, rad[4];
+  if (!fast_schedule(ax.K, &V, &np, rad)) return;
+  const int n = ax.n, K = ax.K, Q2 = 2 * (n / 2 + 1);
+  ax.fast_V = V;
+  ax.fast_npass = np;
+  // four-step twiddles between the two passes: tw4[r][i] = exp(-2 pi i r i / K)
+  // = tw[r i mod K], r < R0, i < K / R0
+  int L = 1;
+  for (int s = 0; s < np; ++s) {
+    ax.fast_radix[s] = rad[s];
+    ax.fast_lprod[s] = L;
+    ax.fast_twofs[s] = 0;
+    L *= rad[s];
+  }
+  ax.tw2.assign(2 * (size_t)K, 0.0);
+  const int R0 = rad[0], KR = K / R0;
+  for (int r = 0; r < R0; ++r)
+    for (int i = 0; i < KR; ++i) {
+      const int j = (r * i) % K;
+      ax.tw2[2 * ((size_t)r * KR + i)] = ax.tw[2 * j];
+      ax.tw2[2 * ((size_t)r * KR + i) + 1] = ax.tw[2 * j + 1];
+    }
+  // G_k[j][l] = the inverse map, frequencies contiguous
+  ax.gmap.assign((size_t)Q2 * n * K, 0.0);
+  for (int k = 0; k < K; ++k)
+    for (int j = 0; j < Q2; ++j)
+      for (int l = 0; l < n; ++l) ax.gmap[((size_t)j * n + l) * K + k] = ax.inv[((size_t)k * Q2 + j) * n + l];
+  ax.invn.assign((size_t)n * K, 0.0);
+  for (int l = 0; l + 1 < n; ++l) ax.invn[(size_t)l * K] = 1.0 / K;
+  for (int k = 1; k < K; ++k)
+    for (int l = 0; l < n; ++l) ax.invn[(size_t)l * K + k] = 1.0 / ax.cnorm[n * k - 1 + l];
+  fast_muk_update(&ax);
 }
 
 }  // namespace femfft
