@@ -164,42 +164,58 @@ def time_steps(torch, fn, steps, warmup, barrier=None):
 APPLY_DF_TRAFFIC_PER_DOF_2D_N9 = 511.0e6 / 21224449
 
 
-def roofline(prof, steps, peaks, wl=None):
-    """Dominant kernel kind of the step and its achieved fraction of its bound."""
+def residual_bytes_per_dof(wl):
+    """Algorithmic HBM bytes of one refinement residual r = b - L u per DOF:
+    read u and b in float64, write r in float32 (20 B, as if fused)."""
+    return 8.0 + 8.0 + 4.0
+
+
+def roofline(prof, steps, peaks, wl=None, residuals_per_step=2):
+    """Dominant kernel kind of the step and its achieved fraction of the HBM
+    roofline: algorithmic bytes (the field reads and writes the method needs,
+    per launch) / the kind's mean CUDA-event launch time / the measured copy
+    bandwidth.  For the double-float residual the algorithmic bytes are the
+    fused residual's 20 B/DOF, spread over the launches of one residual; its
+    float32 lane-operation rate is reported beside it."""
     kind = max(prof, key=lambda k: prof[k]["ms"])
     p = prof[kind]
     if p["launches"] == 0 or p["ms"] <= 0:
         return None, kind
     per_launch_ms = p["ms"] / p["launches"]
     share = p["ms"] / sum(v["ms"] for v in prof.values())
-    if kind == "apply":
-        achieved = p["flops64"] / p["launches"] / (per_launch_ms * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (fp64)",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "apply_kernel (fp64 FMA)",
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe table)",
-                "avg_launch_ms": per_launch_ms, "share_of_step": share}, kind
-    if kind == "apply_df":
+    hbm = peaks.get("hbm_gbs")
+    src = "MEASURED_PEAKS.json hbm_gbs (measured)"
+    if hbm is None:
+        hbm, src = 6800.0, "fallback 6.8 TB/s"
+    out = {"bound": "hbm", "peak": hbm, "unit": "GB/s", "peak_source": src, "avg_launch_ms": per_launch_ms,
+           "share_of_step": share}
+    if kind in ("apply", "apply_df") and wl is not None:
+        dof = 1
+        for k in wl["K"]:
+            dof *= wl["n"] * k - 1
+        launches_per_residual = p["launches"] / max(1, steps * residuals_per_step)
+        alg = residual_bytes_per_dof(wl) * dof / launches_per_residual
+        achieved = alg / (per_launch_ms * 1e-3) / 1e9
         traffic = None
-        if wl is not None and wl["n"] == 9 and len(wl["K"]) == 2:
-            dof = (wl["n"] * wl["K"][0] - 1) * (wl["n"] * wl["K"][1] - 1)
+        if kind == "apply_df" and wl["n"] == 9 and len(wl["K"]) == 2:
             traffic = APPLY_DF_TRAFFIC_PER_DOF_2D_N9 * dof
-        # float32 lane operations of the double-float algorithm against the
-        # float32 issue rate: 152 SMs x 128 lanes x 2.07 GHz (recipe table)
-        achieved = p["flops64"] / p["launches"] / (per_launch_ms * 1e-3) / 1e12
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        gbs = p["bytes"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
-        return {"bound": "alu", "achieved": achieved, "peak": FP32_LANE_TOPS, "unit": "Tops/s (fp32 lanes)",
-                "frac": achieved / FP32_LANE_TOPS, "traffic": traffic,
-                "kernel": "apply_kernel_df (double-float residual)",
-                "peak_source": "152 SMs x 128 fp32 lanes x 2.07 GHz (recipe table)",
-                "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm,
-                "avg_launch_ms": per_launch_ms, "share_of_step": share}, kind
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = p["bytes"] / p["launches"] / (per_launch_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": f"pencil_pass_kernel ({kind})",
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback",
-            "avg_launch_ms": per_launch_ms, "share_of_step": share}, kind
+        out.update({"achieved": achieved, "frac": achieved / hbm, "traffic": traffic,
+                    "algorithmic_bytes_per_launch": alg,
+                    "traffic_over_algorithmic": (traffic / alg) if traffic else None,
+                    "kernel": "apply_kernel_df (double-float refinement residual, "
+                              f"{launches_per_residual:g} launches per residual)"})
+        if kind == "apply_df":
+            lane = p["flops64"] / p["launches"] / (per_launch_ms * 1e-3) / 1e12
+            out["secondary"] = {"fp32_lane_Tops": lane, "fp32_lane_peak_Tops": FP32_LANE_TOPS,
+                                "frac": lane / FP32_LANE_TOPS,
+                                "note": "float32 operations the double-float algorithm executes / "
+                                        "(152 SMs x 128 lanes x 2.07 GHz)"}
+        return out, kind
+    alg = p["bytes"] / p["launches"]
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    out.update({"achieved": achieved, "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": alg,
+                "kernel": f"pencil pass ({kind})"})
+    return out, kind
 
 
 def oracle_full_solve(wl, b):
@@ -553,10 +569,12 @@ def main():
                          f"{t_solve:.1f} s; eigenbasis {t_basis:.1f} s untimed)"}
 
     peaks = _peaks()
-    roof, dom = roofline(prof, args.steps, peaks, wl)
+    roof, dom = roofline(prof, args.steps, peaks, wl, residuals_per_step=args.refine)
     launches = sum(v["launches"] for v in prof.values()) // max(args.steps, 1)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     kernels = {k: {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["ms"] / args.steps,
                    "GB_per_s": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else None,
+                   "hbm_frac": (v["bytes"] / (v["ms"] * 1e-3) / 1e9 / hbm_peak) if v["ms"] else None,
                    ("fp32_Tops" if k == "apply_df" else "fp64_TFLOPs"):
                        (v["flops64"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] and v["flops64"] else None}
                for k, v in prof.items()}

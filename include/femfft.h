@@ -65,7 +65,7 @@ enum fem_fft_status {
   FEM_FFT_ERR_CUDA = -4,          /* CUDA runtime error (message: fem_fft_last_error) */
   FEM_FFT_ERR_TIMEOUT = -5,       /* a bounded device wait expired */
   FEM_FFT_ERR_NOT_CONVERGED = -6, /* refinement stopped above the requested tolerance */
-  FEM_FFT_ERR_NONFINITE = -7      /* NaN or Inf detected in a residual */
+  FEM_FFT_ERR_NONFINITE = -7      /* NaN or Inf in a right-hand side or a residual */
 };
 
 enum fem_fft_precision {
@@ -82,7 +82,8 @@ enum fem_fft_precision {
  * uploads them and allocates the workspace for up to max_nrhs right-hand
  * sides per call (larger nrhs are processed in groups).  Synchronous.
  *   N         number of axes, 1..3
- *   n         element order, 1..9 (the same on every axis)
+ *   n         element order, 1..9, on every axis (per-axis orders:
+ *             fem_fft_plan_create_orders)
  *   h_K[N]    elements per axis; each K_i >= 2 of the form 2^p 3^q with p >= 1
  *   h_X[N]    axis lengths X_i > 0
  *   h_a[N]    coefficients a_i > 0
@@ -96,6 +97,17 @@ enum fem_fft_precision {
  */
 int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, const double* h_X,
                         const double* h_a, double c, int precision, int64_t max_nrhs, void* stream);
+
+/*
+ * fem_fft_plan_create_orders -- as fem_fft_plan_create with an element order
+ * per axis, h_n[N] (each 1..9): Section 4 states the N-D problem with the
+ * 1D spaces S_{K_i}^{(n_i)} of their own orders.  Axis i then has
+ * M_i = n_i K_i - 1 unknowns and its own eigenpairs, transforms and element
+ * matrices; the spectral denominators sum the axes' eigenvalues as before.
+ * Plans with different orders are not accepted by fem_fft_batch_create.
+ */
+int fem_fft_plan_create_orders(fem_fft_plan* out, int N, const int* h_n, const int64_t* h_K, const double* h_X,
+                               const double* h_a, double c, int precision, int64_t max_nrhs, void* stream);
 
 /*
  * fem_fft_plan_set_coefficients -- replace a_i and c of an existing plan
@@ -118,7 +130,12 @@ int fem_fft_plan_destroy(fem_fft_plan plan);
  * max_iter (default 2) refinement steps r = b - L u (float64, matrix-free),
  * u += L^{-1} r (float32 passes), stopping early when the relative residual
  * ||r||_2 / ||b||_2 <= rtol (default 0: always take max_iter steps).  The
- * residual norms are read back at the end of each step only when rtol > 0.
+ * residual norms are read back at the end of each step only when rtol > 0;
+ * then, when the steps run out, the final iterate's residual is evaluated as
+ * well and a value above rtol returns FEM_FFT_ERR_NOT_CONVERGED (u holds the
+ * last iterate).  Non-finite right-hand sides: the first pass flags any NaN
+ * or Inf it reads in b, without synchronising; fem_fft_last_info reports it
+ * (FEM_FFT_ERR_NONFINITE), and with rtol > 0 the solve itself returns it.
  */
 int fem_fft_solve(fem_fft_plan plan, const double* d_b, double* d_u, int64_t nrhs, void* stream);
 
@@ -204,7 +221,10 @@ enum { FEM_FFT_RESIDUAL_F64 = 0, FEM_FFT_RESIDUAL_DF64 = 1 };
 int fem_fft_set_residual_precision(fem_fft_plan plan, int mode);
 
 /* Iterations and relative residual ||b - L u|| / ||b|| of the last MIXED
- * solve whose residual was evaluated (-1 if unknown).  Synchronises. */
+ * solve whose residual was evaluated (-1 if unknown).  Waits for the last
+ * solve on its stream and returns its status: FEM_FFT_ERR_NONFINITE if its
+ * right-hand side held NaN or Inf, FEM_FFT_ERR_NOT_CONVERGED if rtol > 0 was
+ * missed, else FEM_FFT_OK (any precision). */
 int fem_fft_last_info(fem_fft_plan plan, int* iters, double* rel_residual);
 
 /*
@@ -216,6 +236,37 @@ int fem_fft_last_info(fem_fft_plan plan, int* iters, double* rel_residual);
  */
 int fem_fft_forward(fem_fft_plan plan, const double* d_y, double* d_c, int64_t nrhs, void* stream);
 int fem_fft_inverse(fem_fft_plan plan, const double* d_c, double* d_w, int64_t nrhs, void* stream);
+
+/*
+ * fem_fft_forward_fn -- direct F_n-transform along every axis (Section 3,
+ * Theorem 2, item 3): d_w (field) -> d_c, the coefficients w_kl of the
+ * expansion of w in the eigenvectors s_k^(l), w_kl = (calC w, s_k^(l)) /
+ * ||s_k^(l)||_C^2 (calC the N-D mass operator), in the spectral layout above;
+ * the inverse is fem_fft_inverse.  The mass product is folded into the
+ * forward maps as in the theorem's second formula (node sums weighted by
+ * 2 [c_0 + c.p + theta_k (c_n + c.p^)], interior sums by q = C~ p + c; bubble
+ * maps by C~ e), so the transform takes the passes of fem_fft_forward and no
+ * separate mass product.  Float64 path; d_w may equal d_c.
+ */
+int fem_fft_forward_fn(fem_fft_plan plan, const double* d_w, double* d_c, int64_t nrhs, void* stream);
+
+/*
+ * fem_fft_heat_step -- one implicit Euler step of calC u' + L u = b
+ * (Section 4 operator; the heat-equation use of the solver):
+ * (calC + tau L) u_new = calC u + tau b.  The plan must represent
+ * calC + tau L, i.e. be created (or set with fem_fft_plan_set_coefficients)
+ * with coefficients (tau a_i, 1 + tau c); its solve then divides by
+ * 1 + tau (sum_i a_i 4 h_i^-2 lambda_i + c).  The library forms the
+ * right-hand side calC u + tau b (float64 mass product and axpy) and solves.
+ *   tau            > 0, finite
+ *   d_u, d_b       [nrhs][M..] float64 (read)
+ *   d_u_new        [nrhs][M..] float64 (written); distinct from d_u and d_b
+ * FP64 plans and MIXED plans without refinement form the right-hand side in
+ * d_u_new; other MIXED plans in a stream-ordered temporary (cudaMallocAsync,
+ * released on the stream; FEM_FFT_ERR_OOM if it cannot be had).  Asynchronous.
+ */
+int fem_fft_heat_step(fem_fft_plan plan, double tau, const double* d_u, const double* d_b, double* d_u_new,
+                      int64_t nrhs, void* stream);
 
 /*
  * fem_fft_grad_coeffs -- derivatives of a scalar loss through u = L^{-1} f
@@ -236,6 +287,9 @@ int fem_fft_grad_coeffs(fem_fft_plan plan, const double* d_u, const double* d_la
  * for k >= 1 at [k][l-1][:], e^(l) at [0][l-1][:].  Any pointer may be NULL.
  */
 int fem_fft_plan_dims(fem_fft_plan plan, int* N, int* n, int64_t* h_M, int* precision);
+/* the element order of every axis (h_n[N]); fem_fft_plan_dims reports n = 0
+ * when they differ */
+int fem_fft_plan_orders(fem_fft_plan plan, int* h_n);
 int fem_fft_axis_tables(fem_fft_plan plan, int axis, double* h_lam, double* h_cnorm, double* h_p);
 
 /*

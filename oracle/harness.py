@@ -62,11 +62,11 @@ def quad_points(n, K, X, G):
 
 def load_vector(prob, f):
     """f^h for a callable f(x_1, ..., x_N) (vectorised over numpy arrays),
-    (n+1)-point Gauss per axis per element (Section 5)."""
-    n = prob.n
-    G = n + 1
+    (n_i+1)-point Gauss per axis per element (Section 5)."""
     mats, grids = [], []
     for i in range(prob.N):
+        n = prob.ns[i]
+        G = n + 1
         xi, w, pts = quad_points(n, prob.K[i], prob.X[i], G)
         B = _lagrange_eval(n, xi)
         mats.append(_scatter_matrix(n, prob.K[i], G, w[:, None] * B))
@@ -78,7 +78,7 @@ def load_vector(prob, f):
 
 def fine_grid(prob, i):
     """Coordinates of the M_i fine-grid nodes along axis i (x = m h / n)."""
-    return np.arange(1, prob.M[i] + 1) * prob.h[i] / prob.n
+    return np.arange(1, prob.M[i] + 1) * prob.h[i] / prob.ns[i]
 
 
 def nodal_values(prob, u):
@@ -93,11 +93,11 @@ def max_error(prob, uh, u):
 
 def l2_error(prob, uh, u):
     """L2(Omega) error of the FEM function with nodal values uh, by
-    (n+2)-point Gauss per axis per element."""
-    n = prob.n
-    G = n + 2
+    (n_i+2)-point Gauss per axis per element."""
     mats, grids, wts = [], [], []
     for i in range(prob.N):
+        n = prob.ns[i]
+        G = n + 2
         xi, w, pts = quad_points(n, prob.K[i], prob.X[i], G)
         B = _lagrange_eval(n, xi)
         mats.append(_scatter_matrix(n, prob.K[i], G, B).T.tocsr())

@@ -25,17 +25,26 @@ from . import fem1d
 
 
 class Problem:
-    """Static description of one problem: N axes with K_i elements, common
-    order n, lengths X_i, coefficients a_i and c."""
+    """Static description of one problem: N axes with K_i elements of order
+    n_i (Section 4 allows a different order per axis; ``n`` is one int for
+    all axes or one per axis), lengths X_i, coefficients a_i and c.
+    ``self.n`` is the common order (None when the orders differ),
+    ``self.ns`` the per-axis orders."""
 
     def __init__(self, n, K, X=None, a=None, c=0.0):
-        self.n = int(n)
         self.K = tuple(int(k) for k in K)
         self.N = len(self.K)
+        if np.ndim(n) == 0:
+            self.ns = (int(n),) * self.N
+        else:
+            self.ns = tuple(int(x) for x in n)
+            if len(self.ns) != self.N:
+                raise ValueError("one order per axis")
+        self.n = self.ns[0] if len(set(self.ns)) == 1 else None
         self.X = tuple(float(x) for x in (X if X is not None else [1.0] * self.N))
         self.a = tuple(float(x) for x in (a if a is not None else [1.0] * self.N))
         self.c = float(c)
-        self.M = tuple(fem1d.dof_count(self.n, k) for k in self.K)
+        self.M = tuple(fem1d.dof_count(n_i, k) for n_i, k in zip(self.ns, self.K))
         self.h = tuple(x / k for x, k in zip(self.X, self.K))
         self.s = tuple(4.0 / (h * h) for h in self.h)       # 4 h_i^-2
         self._ops = {}
@@ -47,16 +56,16 @@ class Problem:
 
     def basis1d(self, i):
         """(lam, S, cnorm2) of ``fem1d.theorem1_basis`` for axis i (cached per
-        (n, K))."""
-        key = (self.n, self.K[i])
+        (n_i, K_i))."""
+        key = (self.ns[i], self.K[i])
         if key not in self._basis:
-            self._basis[key] = _basis_cache(self.n, self.K[i])
+            self._basis[key] = _basis_cache(self.ns[i], self.K[i])
         return self._basis[key]
 
     def ops1d(self, i):
-        key = (self.n, self.K[i])
+        key = (self.ns[i], self.K[i])
         if key not in self._ops:
-            self._ops[key] = fem1d.assemble(self.n, self.K[i])
+            self._ops[key] = fem1d.assemble(self.ns[i], self.K[i])
         return self._ops[key]
 
     def denominators(self):
@@ -185,7 +194,7 @@ def solve_b(prob, b):
         shape[i - 1] = prob.M[i]
         D = D + (prob.a[i] * prob.s[i] * lam).reshape(shape)
     calA, calC = prob.ops1d(0)
-    n = prob.n
+    n = prob.ns[0]
     alpha = prob.a[0] * prob.s[0]
     M0 = prob.M[0]
     y = np.moveaxis(x, 1, -1).reshape(-1, M0)          # (rhs x later spectral, M0)
@@ -223,7 +232,7 @@ def dirichlet_rhs(prob, g):
         raise ValueError(f"g has shape {x.shape}, expected {ext} or (nrhs,)+{ext}")
     inner = (slice(None),) + (slice(1, -1),) * prob.N
     x[inner] = 0.0
-    full = [fem1d.assemble_full(prob.n, k) for k in prob.K]
+    full = [fem1d.assemble_full(n_i, k) for n_i, k in zip(prob.ns, prob.K)]
     out = np.zeros_like(x)
     for i in range(prob.N + 1):
         t = x
@@ -255,7 +264,7 @@ def heat_step(prob, u, b, tau):
     of L with a_i -> tau a_i and c -> 1 + tau c, so the step is a solve of that
     scaled problem (algorithm (a) with denominators 1 + tau (sum_i a_i 4 h_i^-2
     lambda_i + c))."""
-    scaled = Problem(prob.n, prob.K, prob.X, [tau * a for a in prob.a], 1.0 + tau * prob.c)
+    scaled = Problem(prob.ns, prob.K, prob.X, [tau * a for a in prob.a], 1.0 + tau * prob.c)
     return solve(scaled, mass_apply(prob, u) + tau * np.asarray(b, dtype=np.float64))
 
 

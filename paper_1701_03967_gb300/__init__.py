@@ -29,7 +29,8 @@ def _torch():
 class Plan:
     """A solver plan for one problem shape (owns device tables and workspace).
 
-    n: element order (1..9); K: elements per axis (N = len(K) in 1..3, each K_i
+    n: element order (1..9), one for all axes or one per axis (Section 4);
+    K: elements per axis (N = len(K) in 1..3, each K_i
     even and of the form 2^p 3^q); X: axis lengths; a: per-axis coefficients;
     c: zeroth-order coefficient; precision: "fp64" or "mixed"; max_nrhs:
     right-hand sides per internal group (workspace size)."""
@@ -38,14 +39,20 @@ class Plan:
         torch = _torch()
         L = _lib.lib()
         self.N = len(K)
-        self.n = int(n)
+        if isinstance(n, (tuple, list)):
+            self.ns = tuple(int(x) for x in n)
+            if len(self.ns) != self.N:
+                raise ValueError("one element order per axis")
+        else:
+            self.ns = (int(n),) * self.N
+        self.n = self.ns[0] if len(set(self.ns)) == 1 else None   # the common order, if any
         self.K = tuple(int(k) for k in K)
         self.X = tuple(float(x) for x in (X if X is not None else (1.0,) * self.N))
         self.a = tuple(float(x) for x in (a if a is not None else (1.0,) * self.N))
         self.c = float(c)
         self.precision = precision
         prec = {"fp64": FEM_FFT_FP64, "mixed": FEM_FFT_MIXED}[precision]
-        self.M = tuple(self.n * k - 1 for k in self.K)
+        self.M = tuple(n_i * k - 1 for n_i, k in zip(self.ns, self.K))
         self.dof = 1
         for m in self.M:
             self.dof *= m
@@ -53,8 +60,9 @@ class Plan:
         Xarr = (ctypes.c_double * self.N)(*self.X)
         Aarr = (ctypes.c_double * self.N)(*self.a)
         h = ctypes.c_void_p()
-        _lib.check(L.fem_fft_plan_create(ctypes.byref(h), self.N, self.n, Karr, Xarr, Aarr, self.c, prec,
-                                         int(max_nrhs), self._stream(stream)), "fem_fft_plan_create")
+        Narr = (ctypes.c_int * self.N)(*self.ns)
+        _lib.check(L.fem_fft_plan_create_orders(ctypes.byref(h), self.N, Narr, Karr, Xarr, Aarr, self.c, prec,
+                                                int(max_nrhs), self._stream(stream)), "fem_fft_plan_create_orders")
         self._h = h
         self._torch_device = torch.device("cuda", torch.cuda.current_device())
 
@@ -147,6 +155,15 @@ class Plan:
                    "fem_fft_forward")
         return c
 
+    def forward_fn(self, w, out=None, stream=None):
+        """Direct F_n coefficients along every axis (float64; the mass product
+        folded into the forward maps, Theorem 2 item 3)."""
+        nrhs = self._field(w, "w")
+        c = self._out(w, out)
+        _lib.check(_lib.lib().fem_fft_forward_fn(self._h, w.data_ptr(), c.data_ptr(), nrhs, self._stream(stream)),
+                   "fem_fft_forward_fn")
+        return c
+
     def inverse(self, coef, out=None, stream=None):
         """Inverse F_n-expansion along every axis (float64)."""
         nrhs = self._field(coef, "coef")
@@ -221,7 +238,7 @@ class Plan:
     def axis_tables(self, axis):
         """(lam, cnorm, p) host tables of one axis (numpy arrays)."""
         import numpy as np
-        M, K, n = self.M[axis], self.K[axis], self.n
+        M, K, n = self.M[axis], self.K[axis], self.ns[axis]
         lam = np.zeros(M)
         cn = np.zeros(M)
         p = np.zeros(K * n * max(n - 1, 1))
@@ -371,9 +388,14 @@ class HeatStepper:
                          max_nrhs=max_nrhs, stream=stream)
 
     def step(self, u, b, out=None, stream=None):
-        rhs = self.plan.apply_mass(u, stream=stream)
-        rhs.add_(b, alpha=self.tau)
-        return self.plan.solve(rhs, out=out, stream=stream)
+        """u_new = (C + tau L)^-1 (C u + tau b), all in the library
+        (fem_fft_heat_step)."""
+        nrhs = self.plan._field(u, "u")
+        self.plan._field(b, "b")
+        u_new = self.plan._out(u, out)
+        _lib.check(_lib.lib().fem_fft_heat_step(self.plan._h, self.tau, u.data_ptr(), b.data_ptr(), u_new.data_ptr(),
+                                                nrhs, self.plan._stream(stream)), "fem_fft_heat_step")
+        return u_new
 
     def close(self):
         self.plan.close()

@@ -39,6 +39,8 @@ def lib():
     PI = ctypes.POINTER(ctypes.c_int)
     sig = {
         "fem_fft_plan_create": ([ctypes.POINTER(vp), i32, i32, P64, PD, PD, f64, i32, i64, vp], i32),
+        "fem_fft_plan_create_orders": ([vp, i32, PI, P64, PD, PD, f64, i32, i64, vp], i32),
+        "fem_fft_plan_orders": ([vp, PI], i32),
         "fem_fft_plan_destroy": ([vp], i32),
         "fem_fft_plan_set_coefficients": ([vp, PD, f64, vp], i32),
         "fem_fft_solve": ([vp, vp, vp, i64, vp], i32),
@@ -51,6 +53,8 @@ def lib():
         "fem_fft_set_residual_precision": ([vp, i32], i32),
         "fem_fft_last_info": ([vp, PI, PD], i32),
         "fem_fft_forward": ([vp, vp, vp, i64, vp], i32),
+        "fem_fft_forward_fn": ([vp, vp, vp, i64, vp], i32),
+        "fem_fft_heat_step": ([vp, f64, vp, vp, vp, i64, vp], i32),
         "fem_fft_inverse": ([vp, vp, vp, i64, vp], i32),
         "fem_fft_grad_coeffs": ([vp, vp, vp, i64, PD, PD, vp], i32),
         "fem_fft_plan_dims": ([vp, PI, PI, P64, PI], i32),

@@ -204,6 +204,7 @@ int upload_axis(fem_fft_plan p, const AxisHost& ax, DevTables* d, cudaStream_t s
   if ((rc = upload<T>(p, ax.tw, &d->tw, s))) return rc;
   if ((rc = upload<T>(p, ax.rot, &d->rot, s))) return rc;
   if ((rc = upload<T>(p, ax.fwd, &d->fwd, s))) return rc;
+  if ((rc = upload<T>(p, ax.fwdc, &d->fwdc, s))) return rc;
   if ((rc = upload<T>(p, ax.inv, &d->inv, s))) return rc;
   if ((rc = upload<T>(p, ax.mu, &d->mu, s))) return rc;
   if (ax.fast_V) {
@@ -225,7 +226,7 @@ struct PassPlan {
 
 // Pencils per CTA and the CTA grid for a pass over [outer][M][inner].
 int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inner, bool f64, PassPlan* pp) {
-  const int n = p->n, K = (int)p->K[axis], M = (int)p->M[axis];
+  const int n = p->nax[axis], K = (int)p->K[axis], M = (int)p->M[axis];
   const int Q = n / 2 + 1;
   const size_t csize = f64 ? 2 * sizeof(double) : 2 * sizeof(float);
   PassParams& P = pp->P;
@@ -303,7 +304,7 @@ int plan_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inn
   set_fft_passes(P);
   P.ax.tw = d.tw;
   P.ax.rot = d.rot;
-  P.ax.fwd = d.fwd;
+  P.ax.fwd = p->use_fwdc ? d.fwdc : d.fwd;
   P.ax.inv = d.inv;
   P.ax.mu = d.mu;
   pp->smem = (size_t)W * P.pitch * csize + tables;
@@ -329,7 +330,7 @@ bool fast_eligible(fem_fft_plan p, int mode, int axis, bool f64) {
 
 int plan_fast(fem_fft_plan p, int mode, int axis, long long outer, long long inner, int Wwant, FastPlan* fp) {
   const AxisHost& ax = p->ax[axis];
-  const int n = p->n, K = ax.K, Q = n / 2 + 1, Qp = Q | 1;
+  const int n = ax.n, K = ax.K, Q = n / 2 + 1, Qp = Q | 1;
   const int threads = ax.fast_V == 32 ? fast_threads<32>() : fast_threads<16>();
   FastParams& P = fp->P;
   std::memset(&P, 0, sizeof(P));
@@ -398,6 +399,7 @@ int run_fast(fem_fft_plan p, int mode, int axis, long long outer, long long inne
   FastParams& P = fp.P;
   P.in = in;
   P.out = out;
+  P.nonfinite = (in_f64 && in == p->check_in) ? p->d_flag : nullptr;
   P.in_f64 = in_f64;
   P.out_f64 = out_f64;
   P.accum = accum;
@@ -415,7 +417,7 @@ int run_fast(fem_fft_plan p, int mode, int axis, long long outer, long long inne
   int e;
   {
     ProfScope scope(p, s, kind, bytes, 0.0);
-    e = launch_fast_f32(mode, p->n, P, fp.smem, fp.threads, s);
+    e = launch_fast_f32(mode, p->nax[axis], P, fp.smem, fp.threads, s);
   }
   if (e) return cuda_fail((cudaError_t)e, "pencil pass launch");
   return FEM_FFT_OK;
@@ -434,6 +436,7 @@ int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const
   PassParams& P = pp.P;
   P.in = in;
   P.out = out;
+  P.nonfinite = (in_f64 && in == p->check_in && !p->rec) ? p->d_flag : nullptr;
   P.in_f64 = in_f64;
   P.out_f64 = out_f64;
   P.accum = accum;
@@ -461,8 +464,8 @@ int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const
   int e;
   {
     ProfScope scope(p, s, kind, bytes, 0.0);
-    e = f64 ? launch_pencil_f64(mode, p->n, P, pp.smem, pp.threads, s)
-            : launch_pencil_f32(mode, p->n, P, pp.smem, pp.threads, s);
+    e = f64 ? launch_pencil_f64(mode, p->nax[axis], P, pp.smem, pp.threads, s)
+            : launch_pencil_f32(mode, p->nax[axis], P, pp.smem, pp.threads, s);
   }
   if (e) return cuda_fail((cudaError_t)e, "pencil pass launch");
   return FEM_FFT_OK;
@@ -486,7 +489,7 @@ int run_band(fem_fft_plan p, long long nrhs, bool f64, void* work, cudaStream_t 
   }
   const double elems = (double)nrhs * p->dof;
   // bytes of the three phases: field read + written twice, vertex rows twice
-  const double bytes = elems * (f64 ? 8.0 : 4.0) * (4.0 + 4.0 / p->n);
+  const double bytes = elems * (f64 ? 8.0 : 4.0) * (4.0 + 4.0 / p->nax[0]);
   int e;
   {
     ProfScope scope(p, s, 1, bytes, 0.0);
@@ -501,7 +504,9 @@ int run_band(fem_fft_plan p, long long nrhs, bool f64, void* work, cudaStream_t 
 // the vertex system of the element Schur complement (sigma or D, and off);
 // element data from the interior eigenpairs of the reference matrices.
 int build_band_tables(fem_fft_plan p, cudaStream_t s) {
-  const int n = p->n, n1 = n + 1, NI = n - 1;
+  const int n = p->nax[0], n1 = n + 1, NI = n - 1;
+  const std::vector<double>& A = p->Aref_ax[0];
+  const std::vector<double>& C = p->Cref_ax[0];
   std::vector<double> nu, phi;
   if (interior_eig(n, &nu, &phi)) return FEM_FFT_ERR_ASSUMPTION_A;
   BandParams& B = p->band_proto;
@@ -513,8 +518,6 @@ int build_band_tables(fem_fft_plan p, cudaStream_t s) {
   long long inner = 1;
   for (int j = 1; j < p->N; ++j) inner *= p->M[j];
   B.inner = inner;
-  const std::vector<double>& A = p->Aref;
-  const std::vector<double>& C = p->Cref;
   const int bi[2] = {0, n};
   for (int i = 0; i < NI * NI; ++i) {
     B.phi[i] = phi[i];
@@ -567,10 +570,10 @@ int build_band_tables(fem_fft_plan p, cudaStream_t s) {
     std::vector<ld> pcrow(NI, 0.0L);   // Phi^T Crow_i
     for (int m = 0; m < NI; ++m) {
       ld acc = 0.0L;
-      for (int i = 0; i < NI; ++i) acc += (ld)phi[i * NI + m] * (ld)p->Crow[i + 1];
+      for (int i = 0; i < NI; ++i) acc += (ld)phi[i * NI + m] * (ld)p->Crow_ax[0][i + 1];
       pcrow[m] = acc;
     }
-    ld rowc = (ld)p->Crow[0];          // Crow_0 - E_0i E_ii^-1 Crow_i
+    ld rowc = (ld)p->Crow_ax[0][0];          // Crow_0 - E_0i E_ii^-1 Crow_i
     for (int m = 0; m < NI; ++m) {
       const ld r = 1.0L / (al * (ld)nu[m] + be);
       t[1 + m] = (double)r;
@@ -705,18 +708,25 @@ void pack_even_odd(const std::vector<double>& Mx, int n, double* out) {
   }
 }
 
-// Term t of an apply launch: matrix alpha E + beta E2 where E, E2 are the
-// plan's stiffness (Aref) or mass (Cref) element matrices; its exact row sums
-// are alpha (E 1) + beta (E2 1) with A 1 = 0 and C 1 = Crow.
-void set_mat(ApplyParams& A, int t, const std::vector<double>& E, double alpha, const std::vector<double>* E2,
-             double beta, int n1, const std::vector<double>& Aref, const std::vector<double>& Crow) {
+// Term t of an apply launch along axis P.hax: matrix alpha E + beta E2 where
+// E, E2 name that axis's stiffness (kMatA) or mass (kMatC) element matrix
+// (E2 = 0: none); its exact row sums are alpha (E 1) + beta (E2 1) with
+// A 1 = 0 and C 1 = Crow.
+enum { kMatNone = 0, kMatA = 1, kMatC = 2 };
+void set_mat(fem_fft_plan p, ApplyParams& A, int t, int E, double alpha, int E2, double beta) {
+  const int ax = A.hax;
+  const std::vector<double>& Ar = p->Aref_ax[ax];
+  const std::vector<double>& Cr = p->Cref_ax[ax];
+  const std::vector<double>& Crow = p->Crow_ax[ax];
+  const int n1 = p->nax[ax] + 1;
   std::vector<double> M(n1 * n1);
-  for (int i = 0; i < n1 * n1; ++i) M[i] = alpha * E[i] + (E2 ? beta * (*E2)[i] : 0.0);
+  const std::vector<double>& Em = E == kMatA ? Ar : Cr;
+  const std::vector<double>& E2m = E2 == kMatA ? Ar : Cr;
+  for (int i = 0; i < n1 * n1; ++i) M[i] = alpha * Em[i] + (E2 ? beta * E2m[i] : 0.0);
   pack_even_odd(M, n1 - 1, A.mats[t]);
-  const bool e_is_mass = &E != &Aref;
   for (int r = 0; r < n1; ++r) {
-    double v = e_is_mass ? alpha * Crow[r] : 0.0;
-    if (E2 && E2 != &Aref) v += beta * Crow[r];
+    double v = E == kMatC ? alpha * Crow[r] : 0.0;
+    if (E2 == kMatC) v += beta * Crow[r];
     A.rows1[t][r] = v;
   }
 }
@@ -730,8 +740,9 @@ ApplyParams apply_base(fem_fft_plan p, int axis, long long nrhs) {
   A.outer = outer;
   A.inner = inner;
   A.M = (int)p->M[axis];
-  A.n = p->n;
+  A.n = p->nax[axis];
   A.K = (int)p->K[axis];
+  A.hax = axis;
   return A;
 }
 
@@ -744,9 +755,7 @@ ApplyParams apply_base(fem_fft_plan p, int axis, long long nrhs) {
 // The temporaries p->tmp hold the partial products.
 int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, double* out, const double* b,
                    float* r32, double* norms, cudaStream_t s) {
-  const int N = p->N, n1 = p->n + 1;
-  const std::vector<double>& A = p->Aref;
-  const std::vector<double>& C = p->Cref;
+  const int N = p->N;
   double s_[kMaxN];
   for (int i = 0; i < N; ++i) s_[i] = p->a[i] * 4.0 * p->K[i] * p->K[i] / (p->X[i] * p->X[i]);
   // residual in double-float: every temporary is a double-float field, u and
@@ -767,19 +776,18 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
       P.norms = norms;
     }
   };
-  auto one = [&](int axis, const double* in, double* o, const std::vector<double>& E, double alpha,
-                 const std::vector<double>* E2, double beta) {
+  auto one = [&](int axis, const double* in, double* o, int E, double alpha, int E2, double beta) {
     ApplyParams P = apply_base(p, axis, nrhs);
     P.in[0] = in;
     P.nterm = 1;
     P.nout = 1;
     P.out[0] = o;
-    set_mat(P, 0, E, alpha, E2, beta, n1, p->Aref, p->Crow);
+    set_mat(p, P, 0, E, alpha, E2, beta);
     return P;
   };
   int e;
   if (N == 1) {
-    ApplyParams P = one(0, u, nullptr, A, s_[0], &C, p->c);
+    ApplyParams P = one(0, u, nullptr, kMatA, s_[0], kMatC, p->c);
     finish(P);
     dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
@@ -787,7 +795,7 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
   }
   double *X = p->tmp[0], *Y = p->tmp[1], *Z = p->tmp[2], *W = p->tmp[3];
   {
-    ApplyParams P = one(0, u, X, A, s_[0], &C, p->c);                   // X = E_1 u
+    ApplyParams P = one(0, u, X, kMatA, s_[0], kMatC, p->c);                   // X = E_1 u
     dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
@@ -799,15 +807,15 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
     P.nout = 2;
     P.out[0] = Y;
     P.out[1] = Z;
-    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 0, kMatC, 1.0, kMatNone, 0.0);
     P.t_src[0] = 0; P.t_dst[0] = 0;
-    set_mat(P, 1, A, s_[1], nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 1, kMatA, s_[1], kMatNone, 0.0);
     P.t_src[1] = 1; P.t_dst[1] = 1;
     dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
   if (N == 2) {
-    ApplyParams P = one(0, Z, nullptr, C, 1.0, nullptr, 0.0);          // L u = Y + C_1 Z
+    ApplyParams P = one(0, Z, nullptr, kMatC, 1.0, kMatNone, 0.0);          // L u = Y + C_1 Z
     P.addend = Y;
     finish(P);
     dfify(P);
@@ -815,7 +823,7 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
     return FEM_FFT_OK;
   }
   {
-    ApplyParams P = one(0, Z, Y, C, 1.0, nullptr, 0.0);                 // Y += C_1 Z
+    ApplyParams P = one(0, Z, Y, kMatC, 1.0, kMatNone, 0.0);                 // Y += C_1 Z
     P.addend = Y;
     dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
@@ -828,20 +836,20 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
     P.nout = 2;
     P.out[0] = W;
     P.out[1] = X;
-    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 0, kMatC, 1.0, kMatNone, 0.0);
     P.t_src[0] = 0; P.t_dst[0] = 0;
-    set_mat(P, 1, A, s_[2], nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 1, kMatA, s_[2], kMatNone, 0.0);
     P.t_src[1] = 1; P.t_dst[1] = 1;
     dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
   {
-    ApplyParams P = one(1, X, Z, C, 1.0, nullptr, 0.0);                 // Z = C_2 X
+    ApplyParams P = one(1, X, Z, kMatC, 1.0, kMatNone, 0.0);                 // Z = C_2 X
     dfify(P);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   }
   {
-    ApplyParams P = one(0, Z, nullptr, C, 1.0, nullptr, 0.0);          // L u = W + C_1 Z
+    ApplyParams P = one(0, Z, nullptr, kMatC, 1.0, kMatNone, 0.0);          // L u = W + C_1 Z
     P.addend = W;
     finish(P);
     dfify(P);
@@ -858,9 +866,7 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
 // boundary positions of the other axes; the result's interior is subtracted
 // from b.  Temporaries come from the stream-ordered allocator.
 int dirichlet_chain(fem_fft_plan p, const double* g, double* b, long long nrhs, cudaStream_t s) {
-  const int N = p->N, n1 = p->n + 1;
-  const std::vector<double>& A = p->Aref;
-  const std::vector<double>& C = p->Cref;
+  const int N = p->N;
   double s_[kMaxN];
   long long Mx[kMaxN];
   size_t ext = 1;
@@ -894,17 +900,19 @@ int dirichlet_chain(fem_fft_plan p, const double* g, double* b, long long nrhs, 
     P.bnd = 1;   // the temporaries start at zero (memset below)
     P.bnd_N = N;
     P.bnd_axis = axis;
-    for (int j = 0; j < N; ++j) P.bnd_M[j] = p->M[j];
+    for (int j = 0; j < N; ++j) {
+      P.bnd_M[j] = p->M[j];
+      P.bnd_n[j] = p->nax[j];
+    }
     return P;
   };
-  auto one = [&](int axis, const double* in, double* o, const std::vector<double>& E, double alpha,
-                 const std::vector<double>* E2, double beta) {
+  auto one = [&](int axis, const double* in, double* o, int E, double alpha, int E2, double beta) {
     ApplyParams P = ext_base(axis);
     P.in[0] = in;
     P.nterm = 1;
     P.nout = 1;
     P.out[0] = o;
-    set_mat(P, 0, E, alpha, E2, beta, n1, p->Aref, p->Crow);
+    set_mat(p, P, 0, E, alpha, E2, beta);
     return P;
   };
   auto two = [&](int axis, const double* in0, double* o0, const double* in1, double* o1, double s1) {
@@ -915,9 +923,9 @@ int dirichlet_chain(fem_fft_plan p, const double* g, double* b, long long nrhs, 
     P.nout = 2;
     P.out[0] = o0;
     P.out[1] = o1;
-    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 0, kMatC, 1.0, kMatNone, 0.0);
     P.t_src[0] = 0; P.t_dst[0] = 0;
-    set_mat(P, 1, A, s1, nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 1, kMatA, s1, kMatNone, 0.0);
     P.t_src[1] = 1; P.t_dst[1] = 1;
     return P;
   };
@@ -930,19 +938,19 @@ int dirichlet_chain(fem_fft_plan p, const double* g, double* b, long long nrhs, 
   int e = cudaMemsetAsync(buf, 0, field * nbuf * sizeof(double), s);
   if (!e) e = launch_boundary_only(g, Gz, nrhs, N, Mx, s);
   if (e) rc = cuda_fail((cudaError_t)e, "dirichlet boundary data");
-  run(one(0, Gz, X, A, s_[0], &C, p->c));               // X = E_1 G
+  run(one(0, Gz, X, kMatA, s_[0], kMatC, p->c));               // X = E_1 G
   if (N >= 2) run(two(1, X, Y, Gz, Z, s_[1]));          // Y = C_2 X, Z = a2 s2 A_2 G
   if (N == 2) {
-    ApplyParams P = one(0, Z, X, C, 1.0, nullptr, 0.0);  // T = Y + C_1 Z
+    ApplyParams P = one(0, Z, X, kMatC, 1.0, kMatNone, 0.0);  // T = Y + C_1 Z
     P.addend = Y;
     run(P);
   } else if (N == 3) {
-    ApplyParams P = one(0, Z, Y, C, 1.0, nullptr, 0.0);  // Y += C_1 Z
+    ApplyParams P = one(0, Z, Y, kMatC, 1.0, kMatNone, 0.0);  // Y += C_1 Z
     P.addend = Y;
     run(P);
     run(two(2, Y, W, Gz, X, s_[2]));                     // W = C_3 Y, X = a3 s3 A_3 G
-    run(one(1, X, Z, C, 1.0, nullptr, 0.0));             // Z = C_2 X
-    ApplyParams Q = one(0, Z, Y, C, 1.0, nullptr, 0.0);  // T = W + C_1 Z
+    run(one(1, X, Z, kMatC, 1.0, kMatNone, 0.0));             // Z = C_2 X
+    ApplyParams Q = one(0, Z, Y, kMatC, 1.0, kMatNone, 0.0);  // T = W + C_1 Z
     Q.addend = W;
     run(Q);
     T = Y;
@@ -958,7 +966,7 @@ int dirichlet_chain(fem_fft_plan p, const double* g, double* b, long long nrhs, 
 // out = (prod_i calC_i) u: one mass application per axis, through the
 // temporaries (float64).
 int mass_chain(fem_fft_plan p, const double* u, long long nrhs, double* out, cudaStream_t s) {
-  const int N = p->N, n1 = p->n + 1;
+  const int N = p->N;
   const double* cur = u;
   int e;
   for (int ax = 0; ax < N; ++ax) {
@@ -968,7 +976,7 @@ int mass_chain(fem_fft_plan p, const double* u, long long nrhs, double* out, cud
     P.nout = 1;
     double* dst = ax == N - 1 ? out : p->tmp[ax % 2];
     P.out[0] = dst;
-    set_mat(P, 0, p->Cref, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 0, kMatC, 1.0, kMatNone, 0.0);
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
     cur = dst;
   }
@@ -977,9 +985,7 @@ int mass_chain(fem_fft_plan p, const double* u, long long nrhs, double* out, cud
 
 // dots[i] += lam^T (dL/da_i) u (i < N), dots[N] += lam^T (dL/dc) u
 int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrhs, double* dots, cudaStream_t s) {
-  const int N = p->N, n1 = p->n + 1;
-  const std::vector<double>& A = p->Aref;
-  const std::vector<double>& C = p->Cref;
+  const int N = p->N;
   double s_[kMaxN];
   for (int i = 0; i < N; ++i) s_[i] = 4.0 * p->K[i] * p->K[i] / (p->X[i] * p->X[i]);
   int e;
@@ -988,9 +994,9 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
     P.in[0] = u;
     P.nterm = 2;
     P.nout = 2;
-    set_mat(P, 0, A, s_[0], nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 0, kMatA, s_[0], kMatNone, 0.0);
     P.t_src[0] = 0; P.t_dst[0] = 0;
-    set_mat(P, 1, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 1, kMatC, 1.0, kMatNone, 0.0);
     P.t_src[1] = 0; P.t_dst[1] = 1;
     P.dotv = lam;
     P.dots = dots;
@@ -1004,9 +1010,9 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
     P.nout = 2;
     P.out[0] = p->tmp[0];
     P.out[1] = p->tmp[1];
-    set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 0, kMatC, 1.0, kMatNone, 0.0);
     P.t_src[0] = 0; P.t_dst[0] = 0;
-    set_mat(P, 1, A, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, P, 1, kMatA, 1.0, kMatNone, 0.0);
     P.t_src[1] = 0; P.t_dst[1] = 1;
     if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
     ApplyParams Q = apply_base(p, 0, nrhs);       // s1 A1 t1, s2 C1 t2, C1 t1
@@ -1014,11 +1020,11 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
     Q.in[1] = p->tmp[1];
     Q.nterm = 3;
     Q.nout = 3;
-    set_mat(Q, 0, A, s_[0], nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, Q, 0, kMatA, s_[0], kMatNone, 0.0);
     Q.t_src[0] = 0; Q.t_dst[0] = 0;
-    set_mat(Q, 1, C, s_[1], nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, Q, 1, kMatC, s_[1], kMatNone, 0.0);
     Q.t_src[1] = 1; Q.t_dst[1] = 1;
-    set_mat(Q, 2, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+    set_mat(p, Q, 2, kMatC, 1.0, kMatNone, 0.0);
     Q.t_src[2] = 0; Q.t_dst[2] = 2;
     Q.dotv = lam;
     Q.dots = dots;
@@ -1031,9 +1037,9 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
   P.nout = 2;
   P.out[0] = p->tmp[0];
   P.out[1] = p->tmp[1];
-  set_mat(P, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+  set_mat(p, P, 0, kMatC, 1.0, kMatNone, 0.0);
   P.t_src[0] = 0; P.t_dst[0] = 0;
-  set_mat(P, 1, A, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+  set_mat(p, P, 1, kMatA, 1.0, kMatNone, 0.0);
   P.t_src[1] = 0; P.t_dst[1] = 1;
   if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
   ApplyParams Q = apply_base(p, 1, nrhs);         // w1 = C2 t, w2 = A2 t
@@ -1042,9 +1048,9 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
   Q.nout = 2;
   Q.out[0] = p->tmp[2];
   Q.out[1] = p->tmp[3];
-  set_mat(Q, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+  set_mat(p, Q, 0, kMatC, 1.0, kMatNone, 0.0);
   Q.t_src[0] = 0; Q.t_dst[0] = 0;
-  set_mat(Q, 1, A, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+  set_mat(p, Q, 1, kMatA, 1.0, kMatNone, 0.0);
   Q.t_src[1] = 0; Q.t_dst[1] = 1;
   if ((e = apply_launch(p, Q, s))) return cuda_fail((cudaError_t)e, "apply");
   ApplyParams Q3 = apply_base(p, 1, nrhs);        // w3 = C2 v into tmp[0] (t is dead now)
@@ -1052,7 +1058,7 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
   Q3.nterm = 1;
   Q3.nout = 1;
   Q3.out[0] = p->tmp[0];
-  set_mat(Q3, 0, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+  set_mat(p, Q3, 0, kMatC, 1.0, kMatNone, 0.0);
   Q3.t_src[0] = 0; Q3.t_dst[0] = 0;
   if ((e = apply_launch(p, Q3, s))) return cuda_fail((cudaError_t)e, "apply");
   ApplyParams R = apply_base(p, 0, nrhs);         // s1 A1 w1, s2 C1 w2, s3 C1 w3, C1 w1
@@ -1061,13 +1067,13 @@ int grad_chain(fem_fft_plan p, const double* u, const double* lam, long long nrh
   R.in[2] = p->tmp[0];
   R.nterm = 4;
   R.nout = 4;
-  set_mat(R, 0, A, s_[0], nullptr, 0.0, n1, p->Aref, p->Crow);
+  set_mat(p, R, 0, kMatA, s_[0], kMatNone, 0.0);
   R.t_src[0] = 0; R.t_dst[0] = 0;
-  set_mat(R, 1, C, s_[1], nullptr, 0.0, n1, p->Aref, p->Crow);
+  set_mat(p, R, 1, kMatC, s_[1], kMatNone, 0.0);
   R.t_src[1] = 1; R.t_dst[1] = 1;
-  set_mat(R, 2, C, s_[2], nullptr, 0.0, n1, p->Aref, p->Crow);
+  set_mat(p, R, 2, kMatC, s_[2], kMatNone, 0.0);
   R.t_src[2] = 2; R.t_dst[2] = 2;
-  set_mat(R, 3, C, 1.0, nullptr, 0.0, n1, p->Aref, p->Crow);
+  set_mat(p, R, 3, kMatC, 1.0, kMatNone, 0.0);
   R.t_src[3] = 0; R.t_dst[3] = 3;
   R.dotv = lam;
   R.dots = dots;
@@ -1124,15 +1130,29 @@ int fem_fft_plan_destroy(fem_fft_plan p) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+  if (p->h_flag) cudaFreeHost(p->h_flag);
+  if (p->flag_ev) cudaEventDestroy(p->flag_ev);
   delete p;
   return FEM_FFT_OK;
 }
 
 int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, const double* h_X,
                         const double* h_a, double c, int precision, int64_t max_nrhs, void* stream) {
+  if (N < 1 || N > kMaxN) {
+    if (out) *out = nullptr;
+    return FEM_FFT_ERR_ARG;
+  }
+  const int ns[kMaxN] = {n, n, n};
+  return fem_fft_plan_create_orders(out, N, ns, h_K, h_X, h_a, c, precision, max_nrhs, stream);
+}
+
+int fem_fft_plan_create_orders(fem_fft_plan* out, int N, const int* h_n, const int64_t* h_K, const double* h_X,
+                               const double* h_a, double c, int precision, int64_t max_nrhs, void* stream) {
   if (!out) return FEM_FFT_ERR_ARG;
   *out = nullptr;
-  if (N < 1 || N > kMaxN || n < 1 || n > kMaxOrder || !h_K || !h_X || !h_a || max_nrhs < 1) {
+  bool orders_ok = h_n != nullptr && N >= 1 && N <= kMaxN;
+  for (int i = 0; orders_ok && i < N; ++i) orders_ok = h_n[i] >= 1 && h_n[i] <= kMaxOrder;
+  if (!orders_ok || !h_K || !h_X || !h_a || max_nrhs < 1) {
     g_last_error = "argument out of range";
     return FEM_FFT_ERR_ARG;
   }
@@ -1154,7 +1174,11 @@ int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, con
   fem_fft_plan p = new (std::nothrow) fem_fft_plan_s();
   if (!p) return FEM_FFT_ERR_OOM;
   p->N = N;
-  p->n = n;
+  p->n = h_n[0];
+  for (int i = 0; i < N; ++i) {
+    p->nax[i] = h_n[i];
+    if (h_n[i] != h_n[0]) p->n = 0;   // no common order
+  }
   p->precision = precision;
   p->c = c;
   p->max_nrhs = max_nrhs;
@@ -1163,7 +1187,7 @@ int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, con
     p->K[i] = h_K[i];
     p->X[i] = h_X[i];
     p->a[i] = h_a[i];
-    p->M[i] = n * h_K[i] - 1;
+    p->M[i] = h_n[i] * h_K[i] - 1;
     p->dof *= p->M[i];
   }
   int dev = 0;
@@ -1174,10 +1198,10 @@ int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, con
     return cuda_fail(ce, "device query");
   }
   int rc = FEM_FFT_OK;
-  reference_matrices(n, &p->Aref, &p->Cref, &p->Crow);
+  for (int i = 0; i < N; ++i) reference_matrices(h_n[i], &p->Aref_ax[i], &p->Cref_ax[i], &p->Crow_ax[i]);
   for (int i = 0; i < N && !rc; ++i) {
     // identical axes share nothing on purpose: tables are small
-    if (precompute_axis(n, (int)p->K[i], p->X[i], p->a[i], &p->ax[i])) rc = FEM_FFT_ERR_ASSUMPTION_A;
+    if (precompute_axis(h_n[i], (int)p->K[i], p->X[i], p->a[i], &p->ax[i])) rc = FEM_FFT_ERR_ASSUMPTION_A;
   }
   for (int i = 0; i < N && !rc; ++i) rc = upload_axis<double>(p, p->ax[i], &p->t64[i], s);
   if (precision == FEM_FFT_MIXED)
@@ -1187,8 +1211,23 @@ int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, con
   const int ntmp = N == 1 ? 0 : (N == 2 ? 3 : 4);
   for (int t = 0; t < ntmp && !rc; ++t) rc = dev_alloc(p, (void**)&p->tmp[t], field * sizeof(double));
   if (!rc) rc = dev_alloc(p, (void**)&p->d_scalars, 16 * sizeof(double));
+  if (!rc) rc = dev_alloc(p, (void**)&p->d_flag, sizeof(int));
+  if (!rc && cudaMallocHost((void**)&p->h_flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    rc = FEM_FFT_ERR_OOM;
+  }
+  if (!rc && cudaEventCreateWithFlags(&p->flag_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    rc = FEM_FFT_ERR_CUDA;
+  }
+  if (!rc) {
+    *p->h_flag = 0;
+    if (cudaMemsetAsync(p->d_flag, 0, sizeof(int), s) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "flag");
+  }
   if (rc) {
     for (void* ptr : p->allocs) cudaFree(ptr);
+    if (p->h_flag) cudaFreeHost(p->h_flag);
+    if (p->flag_ev) cudaEventDestroy(p->flag_ev);
     delete p;
     return rc;
   }
@@ -1250,16 +1289,24 @@ int fem_fft_last_info(fem_fft_plan p, int* iters, double* rel) {
   if (!p) return FEM_FFT_ERR_ARG;
   if (iters) *iters = p->last_iters;
   if (rel) *rel = p->last_rel;
-  return FEM_FFT_OK;
+  FEMFFT_CUDA(cudaEventSynchronize(p->flag_ev), "last solve");
+  if (*p->h_flag) return FEM_FFT_ERR_NONFINITE;
+  return p->last_status;
 }
 
 int fem_fft_plan_dims(fem_fft_plan p, int* N, int* n, int64_t* h_M, int* precision) {
   if (!p) return FEM_FFT_ERR_ARG;
   if (N) *N = p->N;
-  if (n) *n = p->n;
+  if (n) *n = p->n;   // 0 when the axes have different orders (fem_fft_plan_orders)
   if (precision) *precision = p->precision;
   if (h_M)
     for (int i = 0; i < p->N; ++i) h_M[i] = p->M[i];
+  return FEM_FFT_OK;
+}
+
+int fem_fft_plan_orders(fem_fft_plan p, int* h_n) {
+  if (!p || !h_n) return FEM_FFT_ERR_ARG;
+  for (int i = 0; i < p->N; ++i) h_n[i] = p->nax[i];
   return FEM_FFT_OK;
 }
 
@@ -1268,7 +1315,7 @@ int fem_fft_axis_tables(fem_fft_plan p, int axis, double* h_lam, double* h_cnorm
   const AxisHost& ax = p->ax[axis];
   if (h_lam) std::memcpy(h_lam, ax.lam.data(), ax.lam.size() * sizeof(double));
   if (h_cnorm) std::memcpy(h_cnorm, ax.cnorm.data(), ax.cnorm.size() * sizeof(double));
-  if (h_p && p->n > 1) std::memcpy(h_p, ax.pvec.data(), (size_t)ax.K * ax.n * (ax.n - 1) * sizeof(double));
+  if (h_p && ax.n > 1) std::memcpy(h_p, ax.pvec.data(), (size_t)ax.K * ax.n * (ax.n - 1) * sizeof(double));
   return FEM_FFT_OK;
 }
 
@@ -1326,38 +1373,69 @@ int fem_fft_solve(fem_fft_plan p, const double* b, double* u, int64_t nrhs, void
     g_last_error = "in-place mixed-precision solve needs max_iter = 0";
     return FEM_FFT_ERR_ARG;
   }
-  int rc;
-  for (int64_t r0 = 0; r0 < nrhs; r0 += p->max_nrhs) {
+  // the first pass of every group raises d_flag on a non-finite b
+  FEMFFT_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), s), "flag");
+  p->last_status = FEM_FFT_OK;
+  int rc = FEM_FFT_OK;
+  for (int64_t r0 = 0; r0 < nrhs && !rc; r0 += p->max_nrhs) {
     const long long cnt = std::min<int64_t>(p->max_nrhs, nrhs - r0);
     const double* bb = b + (size_t)r0 * p->dof;
     double* uu = u + (size_t)r0 * p->dof;
+    p->check_in = bb;
     if (!mixed) {
-      if ((rc = solve_chain(p, true, bb, true, uu, uu, false, cnt, s))) return rc;
+      rc = solve_chain(p, true, bb, true, uu, uu, false, cnt, s);
+      p->check_in = nullptr;
       continue;
     }
-    if ((rc = solve_chain(p, false, bb, true, p->w32, uu, false, cnt, s))) return rc;
+    rc = solve_chain(p, false, bb, true, p->w32, uu, false, cnt, s);
+    p->check_in = nullptr;
+    if (rc) break;
     p->last_iters = 0;
     p->last_rel = -1.0;
-    for (int it = 0; it < p->max_iter; ++it) {
+    // with rtol > 0: the residual of every iterate is read back; when the
+    // steps run out, the last iterate's residual is evaluated too, and a
+    // value above rtol returns FEM_FFT_ERR_NOT_CONVERGED
+    const int evals = p->rtol > 0.0 ? p->max_iter + 1 : p->max_iter;
+    for (int it = 0; it < evals && !rc; ++it) {
       double* norms = nullptr;
       if (p->rtol > 0.0) {
-        FEMFFT_CUDA(cudaMemsetAsync(p->d_scalars, 0, 2 * sizeof(double), s), "memset");
+        if ((rc = cudaMemsetAsync(p->d_scalars, 0, 2 * sizeof(double), s))) {
+          rc = cuda_fail((cudaError_t)rc, "memset");
+          break;
+        }
         norms = p->d_scalars;
       }
-      if ((rc = operator_chain(p, uu, cnt, 1, nullptr, bb, p->w32, norms, s))) return rc;
+      if ((rc = operator_chain(p, uu, cnt, 1, nullptr, bb, p->w32, norms, s))) break;
       if (norms) {
         double h[2];
-        FEMFFT_CUDA(cudaMemcpyAsync(h, p->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, s), "norms");
-        FEMFFT_CUDA(cudaStreamSynchronize(s), "norms sync");
-        if (!std::isfinite(h[0])) return FEM_FFT_ERR_NONFINITE;
+        if (cudaMemcpyAsync(h, p->d_scalars, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+          rc = cuda_fail(cudaGetLastError(), "norms");
+          break;
+        }
+        if (!std::isfinite(h[0]) || !std::isfinite(h[1])) {
+          rc = FEM_FFT_ERR_NONFINITE;
+          break;
+        }
         p->last_rel = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
         if (p->last_rel <= p->rtol) break;
+        if (it == p->max_iter) {
+          p->last_status = FEM_FFT_ERR_NOT_CONVERGED;
+          break;
+        }
       }
-      if ((rc = solve_chain(p, false, p->w32, false, p->w32, uu, true, cnt, s))) return rc;
+      if ((rc = solve_chain(p, false, p->w32, false, p->w32, uu, true, cnt, s))) break;
       p->last_iters = it + 1;
     }
   }
-  return FEM_FFT_OK;
+  p->check_in = nullptr;
+  // the flag reaches the host with the stream (fem_fft_last_info waits for it)
+  if (cudaMemcpyAsync(p->h_flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaEventRecord(p->flag_ev, s) != cudaSuccess) {
+    if (!rc) rc = cuda_fail(cudaGetLastError(), "flag");
+  }
+  if (rc) return rc;
+  return p->last_status;
 }
 
 int fem_fft_apply(fem_fft_plan p, const double* u, double* b, int64_t nrhs, void* stream) {
@@ -1514,6 +1592,52 @@ int fem_fft_forward(fem_fft_plan p, const double* y, double* c, int64_t nrhs, vo
       return rc;
   }
   return FEM_FFT_OK;
+}
+
+int fem_fft_heat_step(fem_fft_plan p, double tau, const double* u, const double* b, double* u_new, int64_t nrhs,
+                      void* stream) {
+  if (p && nrhs == 0) return FEM_FFT_OK;
+  if (!p || !u || !b || !u_new || u_new == u || u_new == b || nrhs < 0 || !(tau > 0.0) || !std::isfinite(tau))
+    return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t total = (size_t)nrhs * p->dof;
+  // the right-hand side C u + tau b is formed in u_new when the solve may run
+  // in place, else in a stream-ordered temporary
+  const bool in_place = p->precision == FEM_FFT_FP64 || p->max_iter == 0;
+  double* rhs = u_new;
+  if (!in_place) {
+    cudaError_t e = cudaMallocAsync((void**)&rhs, total * sizeof(double), s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g_last_error = std::string("cudaMallocAsync: ") + cudaGetErrorString(e);
+      return FEM_FFT_ERR_OOM;
+    }
+  }
+  int rc = FEM_FFT_OK;
+  for (int64_t r0 = 0; r0 < nrhs && !rc; r0 += p->max_nrhs) {
+    const long long cnt = std::min<int64_t>(p->max_nrhs, nrhs - r0);
+    rc = mass_chain(p, u + (size_t)r0 * p->dof, cnt, rhs + (size_t)r0 * p->dof, s);
+  }
+  if (!rc) {
+    const int e = launch_axpy(rhs, b, tau, (long long)total, s);
+    if (e) rc = cuda_fail((cudaError_t)e, "heat step right-hand side");
+  }
+  if (!rc) rc = fem_fft_solve(p, rhs, u_new, nrhs, stream);
+  if (rhs != u_new) cudaFreeAsync(rhs, s);
+  return rc;
+}
+
+int fem_fft_forward_fn(fem_fft_plan p, const double* w, double* c, int64_t nrhs, void* stream) {
+  if (p && nrhs == 0) return FEM_FFT_OK;
+  if (!p || !w || !c || nrhs < 0) return FEM_FFT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = FEM_FFT_OK;
+  p->use_fwdc = 1;
+  for (int ax = p->N - 1; ax >= 0 && !rc; --ax)
+    rc = run_pass(p, MODE_FWD, ax, nrhs, true, ax == p->N - 1 ? (const void*)w : (const void*)c, true, c, true, false,
+                  s);
+  p->use_fwdc = 0;
+  return rc;
 }
 
 int fem_fft_inverse(fem_fft_plan p, const double* c, double* w, int64_t nrhs, void* stream) {

@@ -182,15 +182,14 @@ __device__ __forceinline__ void apply_stage_mats(const ApplyParams& P, ApplySmem
 template <typename I>
 __device__ __forceinline__ bool bnd_live_t(const ApplyParams& P, I o, I w, int e) {
   if (e == 0 || e >= P.K - 2) return true;
-  const I n = (I)P.n;
   for (int j = P.bnd_N - 1; j > P.bnd_axis; --j) {   // axes after the operated one: w, last axis fastest
-    const I m = (I)P.bnd_M[j];
+    const I m = (I)P.bnd_M[j], n = (I)P.bnd_n[j];
     const I i = w % (m + 2);
     w /= m + 2;
     if (i <= n || i + n >= m + 1) return true;
   }
   for (int j = P.bnd_axis - 1; j >= 0; --j) {        // axes before it: o (right-hand side slowest)
-    const I m = (I)P.bnd_M[j];
+    const I m = (I)P.bnd_M[j], n = (I)P.bnd_n[j];
     const I i = o % (m + 2);
     o /= m + 2;
     if (i <= n || i + n >= m + 1) return true;

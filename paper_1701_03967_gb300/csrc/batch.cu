@@ -531,6 +531,13 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
   std::vector<double> work(nprob);
   for (int p = 0; p < nprob; ++p) {
     fem_fft_plan pl = plans[p];
+    bool uniform = pl != nullptr;
+    for (int i = 1; pl && i < pl->N; ++i) uniform = uniform && pl->nax[i] == pl->nax[0];
+    if (pl && !uniform) {
+      // the batched kernel runs every step of a problem in the launch of its
+      // element order; a plan with several orders would span launches
+      return batch_fail(FEM_FFT_ERR_ARG, "batch: plans must have one element order on every axis");
+    }
     if (!pl || pl->precision != FEM_FFT_MIXED || h_nrhs[p] < 1 || h_nrhs[p] > pl->max_nrhs) {
       free_batch(b);
       return batch_fail(FEM_FFT_ERR_ARG, "batch: every plan must be mixed precision with nrhs <= max_nrhs");

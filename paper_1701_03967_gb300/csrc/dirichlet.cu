@@ -83,4 +83,17 @@ int launch_subtract_interior(double* b, const double* t, long long nrhs, int N, 
   return (int)cudaGetLastError();
 }
 
+// y += a x over n float64 values (the tau b term of an implicit Euler
+// right-hand side C u + tau b), grid-stride
+__global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, double a, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = fma(a, x[i], y[i]);
+}
+
+int launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t s) {
+  if (n <= 0) return (int)cudaSuccess;
+  axpy_kernel<<<grid_for(n), kDirThreads, 0, s>>>(y, x, a, n);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace femfft

@@ -23,6 +23,7 @@ struct AxisHost {
   std::vector<double> tw;      // [2K] exp(-2 pi i j / K), (re, im) pairs
   std::vector<double> rot;     // [2K] exp(-i pi k / (2K))
   std::vector<double> fwd;     // [K][n][2Q] per-k forward maps (Q = n/2+1); k = 0: bubble map
+  std::vector<double> fwdc;    // [K][n][2Q] the same for the direct F_n-transform (mass product folded in)
   std::vector<double> inv;     // [K][2Q][n] per-k inverse maps; k = 0: bubble map
   std::vector<double> pvec;    // [K][n][n-1] p_k^(l) (k = 0: e^(l)), for tests
   std::vector<int> parity;     // [n-1] +1 even / -1 odd bubble eigenvector

@@ -79,6 +79,8 @@ struct ApplyParams {
   // loads, products and stores.  bnd_M: interior extents of all axes.
   int bnd, bnd_N, bnd_axis;
   long long bnd_M[kMaxN];
+  int bnd_n[kMaxN];              // element orders of all axes (layer depths)
+  int hax;                       // host bookkeeping: the operated axis (kernels ignore it)
 };
 
 // Tile width TW of the apply kernels (a block covers TW positions times
@@ -121,6 +123,8 @@ int launch_apply(const ApplyParams& P, cudaStream_t s);
 // each end of every axis (extents M_i + 2, C order, nrhs leading)
 int launch_boundary_only(const double* g, double* gz, long long nrhs, int N, const long long* M, cudaStream_t s);
 int launch_subtract_interior(double* b, const double* t, long long nrhs, int N, const long long* M, cudaStream_t s);
+// y += a x over n float64 values (dirichlet.cu)
+int launch_axpy(double* y, const double* x, double a, long long n, cudaStream_t s);
 
 // Algorithm (b) along axis 0 (band.cu): the 1D problems
 // [alpha calA + beta_w calC] v = y, one per position w of the later axes, on

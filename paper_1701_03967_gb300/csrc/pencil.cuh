@@ -110,6 +110,7 @@ struct PassParams {
   int pstride[kMaxRadixPasses];
   int kshift;        // log2 K when K is a power of two, else -1 (set_fft_passes)
   int in_f64, out_f64, accum;
+  int* nonfinite;    // if set: raised (atomicOr 1) when a float64 input value is NaN or Inf
 };
 
 // c = q * d + r for the divisors K and K / 2 of the pass, by shifts when K
@@ -309,7 +310,9 @@ __device__ __forceinline__ S ld_field(const S* p) {
 // are adjacent in memory, so thread t serves pencil t mod W (W is a power of
 // two dividing the block size).  Loads are issued kLoadBatch at a time.
 template <typename T, int NORD, bool NC>
-__device__ void load_tile(T* smr, const PassParams& P, long long tile, bool spectral) {
+__device__ bool load_tile(T* smr, const PassParams& P, long long tile, bool spectral) {
+  bool nf = false;   // a float64 input value that is not finite
+  const bool check = P.nonfinite != nullptr;
   constexpr int Q2 = 2 * (NORD / 2 + 1);
   const PassGeom& g = P.g;
   const int M = g.M;
@@ -325,7 +328,11 @@ __device__ void load_tile(T* smr, const PassParams& P, long long tile, bool spec
           const int i = i0 + u * blockDim.x;
           v[u] = T(0);
           if (i < M && base >= 0) {
-            if (P.in_f64) v[u] = T(ld_field<NC>(reinterpret_cast<const double*>(P.in) + base + i));
+            if (P.in_f64) {
+              const double x = ld_field<NC>(reinterpret_cast<const double*>(P.in) + base + i);
+              if (check) nf |= !isfinite(x);
+              v[u] = T(x);
+            }
             else v[u] = T(ld_field<NC>(reinterpret_cast<const float*>(P.in) + base + i));
           }
         }
@@ -336,7 +343,7 @@ __device__ void load_tile(T* smr, const PassParams& P, long long tile, bool spec
         }
       }
     }
-    return;
+    return nf;
   }
   const int W = g.W;
   const int p = threadIdx.x & (W - 1);
@@ -352,7 +359,11 @@ __device__ void load_tile(T* smr, const PassParams& P, long long tile, bool spec
       v[u] = T(0);
       if (i < M && base >= 0) {
         const long long off = base + (long long)i * stride;
-        if (P.in_f64) v[u] = T(ld_field<NC>(reinterpret_cast<const double*>(P.in) + off));
+        if (P.in_f64) {
+          const double x = ld_field<NC>(reinterpret_cast<const double*>(P.in) + off);
+          if (check) nf |= !isfinite(x);
+          v[u] = T(x);
+        }
         else v[u] = T(ld_field<NC>(reinterpret_cast<const float*>(P.in) + off));
       }
     }
@@ -362,6 +373,7 @@ __device__ void load_tile(T* smr, const PassParams& P, long long tile, bool spec
       if (i < M) dst[chunk_slot<NORD, Q2>(i + sh)] = v[u];
     }
   }
+  return nf;
 }
 
 template <typename T, bool NC>
@@ -726,11 +738,11 @@ __device__ __forceinline__ void pencil_tile(const PassParams& P, long long tile,
   constexpr bool DIVIDE = MODE == MODE_FUSED || MODE == MODE_FWD_DIV;
   if (DIVIDE && threadIdx.x < P.g.W) base[threadIdx.x] = pencil_den_base<T, NORD>(P, tile, threadIdx.x);
   if (MODE == MODE_INV) {
-    load_tile<T, NORD, NC>(smr, P, tile, true);
-    __syncthreads();
+    const bool nf = load_tile<T, NORD, NC>(smr, P, tile, true);
+    if (__syncthreads_or(nf) && threadIdx.x == 0 && P.nonfinite) atomicOr(P.nonfinite, 1);
   } else {
-    load_tile<T, NORD, NC>(smr, P, tile, false);
-    __syncthreads();
+    const bool nf = load_tile<T, NORD, NC>(smr, P, tile, false);
+    if (__syncthreads_or(nf) && threadIdx.x == 0 && P.nonfinite) atomicOr(P.nonfinite, 1);
     build_sequences<T, NORD>(sm, P);
     fft_all<T, Q>(sm, P, tw, P.g.W * Q, true, false);
     post_twiddle<T, NORD>(sm, P, rot);

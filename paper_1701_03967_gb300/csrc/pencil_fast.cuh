@@ -70,6 +70,7 @@ struct FastParams {
   DivideDev dv;
   int in_f64, out_f64, accum;
   int ahead;           // L2 prefetch distance in tiles (the resident CTAs of the grid; 0: none)
+  int* nonfinite;      // if set: raised (atomicOr 1) when a float64 input value is NaN or Inf
 };
 
 // ------------------------------------------------------------ DFT kernels
@@ -325,10 +326,13 @@ __device__ __forceinline__ void fast_copy_wait() { asm volatile("cp.async.wait_a
 // are swept by the whole block; the W pencils of a strided tile are adjacent
 // in memory, thread t serving pencil t mod W.  float32 fields are copied
 // with cp.async, the whole tile in flight at once; float64 fields (rounded
-// to T) go through registers, LB loads in flight per thread.  Elements of
-// pencils beyond the array are not loaded (their results are not stored).
+// to T) go through registers, LB loads in flight per thread, and are checked
+// for NaN and Inf (the return value).  Elements of pencils beyond the array
+// are not loaded (their results are not stored).
 template <typename T, int NORD, bool NC, int LB>
-__device__ void fast_load(T* smr, const FastParams& P, long long tile, bool spectral) {
+__device__ bool fast_load(T* smr, const FastParams& P, long long tile, bool spectral) {
+  bool nf = false;   // a float64 input value that is not finite
+  const bool check = P.nonfinite != nullptr;
   const PassGeom& g = P.g;
   constexpr int Q2p = 2 * ((NORD / 2 + 1) | 1);
   const int M = g.M, P2 = 2 * P.pitch;
@@ -350,7 +354,11 @@ __device__ void fast_load(T* smr, const FastParams& P, long long tile, bool spec
 #pragma unroll
         for (int u = 0; u < LB; ++u) {
           const int i = i0 + u * blockDim.x;
-          if (i < M) v[u] = T(ld_field<NC>(ind + base + i));
+          if (i < M) {
+            const double x = ld_field<NC>(ind + base + i);
+            if (check) nf |= !isfinite(x);
+            v[u] = T(x);
+          }
         }
 #pragma unroll
         for (int u = 0; u < LB; ++u) {
@@ -360,7 +368,7 @@ __device__ void fast_load(T* smr, const FastParams& P, long long tile, bool spec
       }
     }
     if (async) fast_copy_wait();
-    return;
+    return nf;
   }
   const int W = g.W;
   const int p = threadIdx.x & (W - 1);
@@ -368,19 +376,23 @@ __device__ void fast_load(T* smr, const FastParams& P, long long tile, bool spec
   const long long base = pencil_base(g, tile, p);
   const long long stride = g.inner;
   T* dst = smr + p * P2;
-  if (base < 0) return;
+  if (base < 0) return nf;
   if (async) {
     for (int i = threadIdx.x / W; i < M; i += istep)
       fast_copy4(dst + fast_slot<NORD, Q2p>(i + sh), inf + base + (long long)i * stride);
     fast_copy_wait();
-    return;
+    return nf;
   }
   for (int i0 = threadIdx.x / W; i0 < M; i0 += LB * istep) {
     T v[LB];
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
       const int i = i0 + u * istep;
-      if (i < M) v[u] = T(ld_field<NC>(ind + base + (long long)i * stride));
+      if (i < M) {
+        const double x = ld_field<NC>(ind + base + (long long)i * stride);
+        if (check) nf |= !isfinite(x);
+        v[u] = T(x);
+      }
     }
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
@@ -388,6 +400,7 @@ __device__ void fast_load(T* smr, const FastParams& P, long long tile, bool spec
       if (i < M) dst[fast_slot<NORD, Q2p>(i + sh)] = v[u];
     }
   }
+  return nf;
 }
 
 // Shared -> global.  With accumulation (u += result) the old values are
@@ -772,12 +785,13 @@ __device__ __forceinline__ void fast_tile(const FastParams& P, long long tile, u
     Pd.dv = P.dv;
     den_base[threadIdx.x] = pencil_den_base<T, NORD>(Pd, tile, threadIdx.x);
   }
+  // the barrier after the load also ORs the non-finite checks of the block
   if (MODE == MODE_INV) {
-    fast_load<T, NORD, NC, LB>(smr, P, tile, true);
-    __syncthreads();
+    const bool nf = fast_load<T, NORD, NC, LB>(smr, P, tile, true);
+    if (__syncthreads_or(nf) && threadIdx.x == 0 && P.nonfinite) atomicOr(P.nonfinite, 1);
   } else {
-    fast_load<T, NORD, NC, LB>(smr, P, tile, false);
-    __syncthreads();
+    const bool nf = fast_load<T, NORD, NC, LB>(smr, P, tile, false);
+    if (__syncthreads_or(nf) && threadIdx.x == 0 && P.nonfinite) atomicOr(P.nonfinite, 1);
     fast_build<T, NORD>(sm, P);
     fast_fft<T, Q, V, true, false>(sm, P);
     __syncthreads();

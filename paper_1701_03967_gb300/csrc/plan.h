@@ -18,6 +18,7 @@ struct DevTables {
   void* tw = nullptr;
   void* rot = nullptr;
   void* fwd = nullptr;
+  void* fwdc = nullptr;   // forward maps of the direct F_n-transform
   void* inv = nullptr;
   void* mu = nullptr;
   // register-radix passes (pencil_fast.cuh); null when the axis is not eligible
@@ -82,8 +83,9 @@ struct fem_fft_plan_s {
   int64_t max_nrhs = 1, dof = 0;
   femfft::AxisHost ax[femfft::kMaxN];
   femfft::DevTables t64[femfft::kMaxN], t32[femfft::kMaxN];
-  std::vector<double> Aref, Cref;      // element matrices
-  std::vector<double> Crow;            // exact row sums of Cref (those of Aref are 0)
+  int nax[femfft::kMaxN] = {0, 0, 0};  // element order of every axis (n: the common order, 0 if they differ)
+  std::vector<double> Aref_ax[femfft::kMaxN], Cref_ax[femfft::kMaxN];   // element matrices per axis
+  std::vector<double> Crow_ax[femfft::kMaxN];   // exact row sums of Cref_ax (those of Aref_ax are 0)
   float* w32 = nullptr;                // mixed workspace [max_nrhs][dof]
   double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};   // float64 temporaries
   double* d_scalars = nullptr;         // device scalars (norms, dots)
@@ -105,6 +107,16 @@ struct fem_fft_plan_s {
   // float passes on the register-radix kernels where the axis allows it
   // (fem_fft_set_pass_kernels); pencils per tile chosen by fem_fft_plan_tune
   int fast_passes = 1;
+  // forward passes read the direct F_n-transform maps (fem_fft_forward_fn)
+  int use_fwdc = 0;
+  // non-finite input detection: the first pass of a solve that reads the
+  // caller's right-hand side (check_in) raises d_flag; the flag is copied to
+  // pinned h_flag at the end of the solve (event flag_ev)
+  int* d_flag = nullptr;
+  int* h_flag = nullptr;
+  cudaEvent_t flag_ev = nullptr;
+  const void* check_in = nullptr;
+  int last_status = 0;                 // FEM_FFT_OK or FEM_FFT_ERR_NOT_CONVERGED of the last solve
   int fast_W[3][femfft::kMaxN] = {{0}};
   // algorithm (b) of Section 4 (fem_fft_set_algorithm): band-solve tables
   // per position of the later axes (float64 and float32 copies), the element

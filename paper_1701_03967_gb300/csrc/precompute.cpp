@@ -330,7 +330,15 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
   ax.rot.assign(2 * K, 0.0);
   const int Q2 = 2 * Q;              // reals per chunk: (sine, cosine) pairs
   ax.fwd.assign((size_t)K * n * Q2, 0.0);
+  ax.fwdc.assign((size_t)K * n * Q2, 0.0);
   ax.inv.assign((size_t)K * Q2 * n, 0.0);
+  // partition of the reference mass matrix (Section 2): C = [c0 c^T cn; c C~ c^; cn c^T c0]
+  std::vector<dd> cvec(std::max(n - 1, 1)), Ct_(std::max((n - 1) * (n - 1), 1));
+  for (int i = 0; i + 1 < n; ++i) {
+    cvec[i] = C[(i + 1) * n1 + 0];
+    for (int j = 0; j + 1 < n; ++j) Ct_[i * (n - 1) + j] = C[(i + 1) * n1 + (j + 1)];
+  }
+  const dd c0 = C[0], cn = C[n];
   ax.pvec.assign((size_t)K * n * std::max(n - 1, 1), 0.0);
   ax.parity.assign(std::max(n - 1, 0), 0);
 
@@ -371,6 +379,15 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
       ax.lam[l] = lam0[l].to_double();
       ax.cnorm[l] = double(K);
       for (int i = 0; i < m; ++i) ax.pvec[(size_t)l * (n - 1) + i] = E[i * m + l].to_double();
+      // direct F_n-transform (Theorem 2, item 3): (C w, s_0) = (C~ sum_j (-P)^{j-1} w_{j-1/2}) . e,
+      // i.e. the bubble map with C~ e in place of e
+      double* fbc = &ax.fwdc[0];
+      for (int q = 1; q < Q; ++q) {
+        dd ce(0.0);
+        for (int i = 0; i < m; ++i) ce += Ct_[(q - 1) * m + i] * E[i * m + l];
+        if (par > 0) fbc[l * Q2 + 2 * q] = (ce / dd(double(K))).to_double();
+        else if (q < QC) fbc[l * Q2 + 2 * q + 1] = (ce / dd(double(K))).to_double();
+      }
       // forward: y_0l = (1/K) sum_m e[m] S_m(K) (even e) or sum_m e[m] C_m(0) (odd e)
       // inverse: a_m(K) = b_e[m], b_m(0) = b_o[m] with b = sum_l w_0l e^(l)
       for (int q = 1; q < Q; ++q) {
@@ -434,6 +451,28 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
       dd inv_n = dd(1.0) / nrm;
       F[l * Q2 + 0] = (chh * inv_n * dd(0.25)).to_double();
       F[l * Q2 + 1] = (sh * inv_n * dd(0.25)).to_double();
+      {
+        // direct F_n-transform (Theorem 2, item 3, second formula): the node
+        // sum weighted by 2 [c0 + c.p + theta (cn + c.p^)] and p replaced by
+        // q = C~ p + c in the interior sums
+        double* FC = &ax.fwdc[(size_t)k * n * Q2];
+        dd cp(0.0), cpc(0.0);
+        std::vector<dd> qz(n + 1, dd(0.0));   // qz[1..n-1] = q (1-based like z)
+        for (int i = 0; i + 1 < n; ++i) {
+          cp += cvec[i] * z[i + 1];
+          cpc += cvec[i] * z[n - 1 - i];
+          dd acc = cvec[i];
+          for (int j = 0; j + 1 < n; ++j) acc += Ct_[i * (n - 1) + j] * z[j + 1];
+          qz[i + 1] = acc;
+        }
+        const dd gam = dd(2.0) * (c0 + cp + theta * (cn + cpc));
+        FC[l * Q2 + 0] = (gam * chh * inv_n * dd(0.25)).to_double();
+        FC[l * Q2 + 1] = (gam * sh * inv_n * dd(0.25)).to_double();
+        for (int q = 1; q < Q; ++q) {
+          FC[l * Q2 + 2 * q] = (chh * ((qz[q] + qz[n - q]) * dd(0.5)) * inv_n).to_double();
+          if (q < QC) FC[l * Q2 + 2 * q + 1] = (-(sh * ((qz[q] - qz[n - q]) * dd(0.5)) * inv_n)).to_double();
+        }
+      }
       I[0 * n + l] = 0.5 * cphi;
       I[1 * n + l] = 0.5 * sphi;
       for (int q = 1; q < Q; ++q) {
@@ -447,7 +486,6 @@ int precompute_axis(int n, int K, double X, double a, AxisHost* out) {
         }
       }
     }
-    (void)theta;
   }
   for (int i = 0; i < M; ++i) ax.mu[i] = a * ax.s * ax.lam[i];
   fast_tables(&ax);

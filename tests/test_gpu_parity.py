@@ -131,6 +131,35 @@ def test_forward_and_inverse_transforms_match_oracle(case):
     assert _relmax(got_w, osolve.inverse_expansion(prob, w)) <= 1e-12
 
 
+@pytest.mark.parametrize("case", CASES[::3] + [dict(n=1, K=(12,), c=0.5), dict(n=8, K=(6, 4), c=0.0)],
+                         ids=lambda c: f"n{c['n']}_K{'x'.join(map(str, c['K']))}")
+def test_direct_fn_transform_matches_oracle(case):
+    """Direct F_n-transform (Theorem 2, item 3), the mass product folded into
+    the forward maps: equals the FC_n coefficients of calC w (the oracle's
+    dense eigenbasis products of its mass operator), and the inverse F_n
+    transform of it returns w."""
+    prob = _prob(case)
+    w = synth.normal_batch(2, prob.M, synth.CFG_TEST, 106)
+    plan = _plan(case, "fp64")
+    wt = torch.from_numpy(w).cuda()
+    got = plan.forward_fn(wt).cpu().numpy()
+    want = osolve.forward_coefficients(prob, osolve.mass_apply(prob, w))
+    sg = _bubble_signs(plan, prob)
+    S = np.ones(prob.M)
+    for i, s_ in enumerate(sg):
+        shape = [1] * prob.N
+        shape[i] = prob.M[i]
+        S = S * s_.reshape(shape)
+    assert _rel(got * S, want) <= 1e-12
+    assert _relmax(got * S, want) <= 1e-12
+    back = plan.inverse(torch.from_numpy(got).cuda()).cpu().numpy()
+    assert _rel(back, w) <= 1e-12
+    assert _relmax(back, w) <= 1e-12
+    # in place
+    plan.forward_fn(wt, out=wt)
+    assert _rel(wt.cpu().numpy(), got) <= 1e-15
+
+
 def test_manufactured_solution_error_matches_paper_table():
     """2D, n=5, K=16: max-norm error 5.4e-8 (Section 5 table, algorithm (a))."""
     u, f = harness.manufactured(harness.PAPER_2D, 2, (1, 1), 1.0)

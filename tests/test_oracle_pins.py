@@ -168,6 +168,10 @@ CASES = [
     dict(n=1, K=(5, 7), X=(1.0, 1.0), a=(1.0, 1.0), c=0.0),
     dict(n=2, K=(3, 3, 4), X=(1.0, 1.2, 0.9), a=(1.0, 2.0, 0.5), c=0.3),
     dict(n=3, K=(2, 3, 2), X=(1.0, 1.0, 1.0), a=(1.0, 1.0, 1.0), c=0.0),
+    # per-axis orders n_i (Section 4)
+    dict(n=(3, 7), K=(4, 3), X=(1.0, 2.0), a=(1.0, 2.5), c=1.0),
+    dict(n=(2, 5, 9), K=(3, 2, 2), X=(1.0, 0.7, 1.2), a=(0.8, 1.3, 2.0), c=0.2),
+    dict(n=(1, 4), K=(6, 3), X=(1.5, 1.0), a=(1.0, 1.0), c=-1.0),
 ]
 
 
@@ -195,7 +199,7 @@ def test_heat_step_matches_dense_implicit_euler(case):
     tau = 0.013
     C = np.ones((1, 1))
     for i in range(p.N):
-        C = np.kron(C, fem1d.assemble(p.n, p.K[i])[1])
+        C = np.kron(C, fem1d.assemble(p.ns[i], p.K[i])[1])
     L = solve.assemble_dense(p)
     rhs = (C @ u.reshape(2, -1).T + tau * b.reshape(2, -1).T)
     want = np.linalg.solve(C + tau * L, rhs).T.reshape(u.shape)
@@ -213,7 +217,7 @@ def test_heat_step_decays_eigenmodes_exactly():
     tau = 0.05
     vecs, lams = [], []
     for i, pick in enumerate((2, 7)):
-        calA, calC = fem1d.assemble(p.n, p.K[i])
+        calA, calC = fem1d.assemble(p.ns[i], p.K[i])
         w, V = scipy.linalg.eigh(calA, calC)
         vecs.append(V[:, pick])
         lams.append(w[pick])
@@ -356,23 +360,27 @@ def test_full_assembly_structure():
 
 DIRICHLET_CASES = [dict(n=2, K=(3, 4), X=(1.0, 1.5), a=(1.3, 0.7), c=0.4),
                    dict(n=3, K=(2, 3, 2), X=(1.0, 0.8, 1.2), a=(0.9, 1.1, 2.0), c=0.0),
-                   dict(n=4, K=(5,), X=(2.0,), a=(2.0,), c=1.5)]
+                   dict(n=4, K=(5,), X=(2.0,), a=(2.0,), c=1.5),
+                   dict(n=(2, 5), K=(3, 2), X=(1.0, 1.5), a=(1.3, 0.7), c=0.4),
+                   dict(n=(4, 1, 3), K=(2, 4, 2), X=(1.0, 0.8, 1.2), a=(0.9, 1.1, 2.0), c=0.3)]
 
 
-@pytest.mark.parametrize("case", DIRICHLET_CASES, ids=[f"n{c['n']}_{len(c['K'])}d" for c in DIRICHLET_CASES])
+@pytest.mark.parametrize("case", DIRICHLET_CASES,
+                         ids=[f"n{'_'.join(map(str, np.atleast_1d(c['n'])))}_{len(c['K'])}d" for c in DIRICHLET_CASES])
 def test_dirichlet_data_reproduce_polynomials(case):
     """Section 4 with non-zero boundary values: when the exact solution is a
-    polynomial of degree <= n in every variable it lies in the FEM space, so
+    polynomial of degree <= n_i in variable i it lies in the FEM space, so
     the Galerkin solution equals it; the load vector of its right-hand side
     -sum a_i u_ii + c u is exact with (n+1)-point Gauss (Section 5).  So the
     solve with the boundary correction must return u at every interior node,
     whatever the coefficients; a dropped term, a wrong sign or a wrong
     coupling in the correction breaks the equality."""
-    n, N = case["n"], len(case["K"])
-    prob = solve.Problem(n, case["K"], case["X"], case["a"], case["c"])
+    N = len(case["K"])
+    prob = solve.Problem(case["n"], case["K"], case["X"], case["a"], case["c"])
+    ns = prob.ns
     rng = np.random.default_rng(11)
-    P = [np.polynomial.Polynomial(rng.uniform(-1, 1, n + 1)) for _ in range(N)]
-    Qp = [np.polynomial.Polynomial(rng.uniform(-1, 1, n + 1)) for _ in range(N)]
+    P = [np.polynomial.Polynomial(rng.uniform(-1, 1, ns[i] + 1)) for i in range(N)]
+    Qp = [np.polynomial.Polynomial(rng.uniform(-1, 1, ns[i] + 1)) for i in range(N)]
 
     def u(*x):
         prod = np.ones_like(x[0])
@@ -391,7 +399,7 @@ def test_dirichlet_data_reproduce_polynomials(case):
         return out
 
     b = harness.load_vector(prob, f)
-    ext_grid = [np.arange(prob.M[i] + 2) * prob.h[i] / n for i in range(N)]
+    ext_grid = [np.arange(prob.M[i] + 2) * prob.h[i] / ns[i] for i in range(N)]
     g = u(*np.meshgrid(*ext_grid, indexing="ij"))
     got = solve.solve_dirichlet(prob, b, g)
     want = harness.nodal_values(prob, u)
