@@ -114,24 +114,23 @@ def job_value(units_per_rank, world_size, ms):
 
 
 def time_pipeline(torch, plan, bh, uh, steps, warmup, barrier=None):
-    """ms per step of host-to-host solves through HostSolveStream: every
-    step uploads bh, solves and downloads into uh; the timed region runs from
-    an event before the first upload to the last download."""
-    from paper_1701_03967_gb300 import HostSolveStream
-    pipe = HostSolveStream(plan, depth=2)
+    """ms per step of host-to-host solves through the C ABI's host-buffer
+    path (fem_fft_solve_host): every step uploads bh, solves and downloads into
+    uh, the copies pipelined with neighbouring solves inside the library; the
+    timed region runs from an event before the first call to the wait for the
+    last download (fem_fft_host_wait)."""
     for _ in range(warmup):
-        pipe.submit(bh, uh)
-    pipe.synchronize()
+        plan.solve_host(bh, uh)
+    plan.host_wait()
     torch.cuda.synchronize()
     if barrier:
         barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
-    pipe.start_after(ev0)
     for _ in range(steps):
-        pipe.submit(bh, uh)
-    pipe.wait()
+        plan.solve_host(bh, uh)
+    plan.host_wait()
     ev1.record()
     torch.cuda.synchronize()
     if barrier:
@@ -377,14 +376,15 @@ def run_other_workloads(torch, args, barrier):
 
 def transform_sweep(torch, args, barrier, g, n=5):
     """The 1D transform timing of Section 5 (direct FC_n and inverse F_n
-    transforms, n = 5, K from 2^5 up, powers of two and composites): float64
+    transforms, n = 5, K = 2^5 .. 2^20 and 3 2^4 .. 3 2^17): float64
     transforms of a batch of pencils of 2^24 unknowns in all, reported per
-    transform.  K whose pencil does not fit one CTA's shared memory is listed
-    as refused (the kernels keep a whole pencil on chip)."""
+    transform.  Pencils that fit one CTA's shared memory take the on-chip
+    passes, longer ones the global four-step path.  A K the planner refuses
+    is listed as refused."""
     from paper_1701_03967_gb300 import FemFftError, Plan
     steps = max(2, args.steps // 2)
     out = {}
-    Ks = [2 ** p for p in range(5, 15)] + [3 * 2 ** p for p in range(4, 13)]
+    Ks = [2 ** p for p in range(5, 21)] + [3 * 2 ** p for p in range(4, 18)]
     for K in sorted(Ks):
         M = n * K - 1
         nrhs = max(1, (1 << 24) // M)
@@ -543,8 +543,8 @@ def main():
         mixed.solve(b, out=u)
         uh.copy_(u, non_blocking=True)
     ms_e2e_serial = time_steps(torch, e2e_step, args.steps, args.warmup, barrier)
-    # the same solves pipelined: step k+1's upload and step k-1's download run
-    # on their own streams under step k's solve (HostSolveStream, two buffer pairs)
+    # the same solves through the library's host-buffer entry point: step k+1's
+    # upload and step k-1's download run on its copy streams under step k's solve
     ms_e2e = time_pipeline(torch, mixed, bh, uh, args.steps, args.warmup, barrier)
     clk = clocks.stop()
 
@@ -591,8 +591,9 @@ def main():
         "accuracy": acc,
         "e2e": {"value": job_value(dof, ws, ms_e2e), "unit": "DOF/s", "h2d_bytes_per_step": dof * 8,
                 "d2h_bytes_per_step": dof * 8, "ms_per_step": ms_e2e,
-                "method": "HostSolveStream: pinned host b -> device, solve, device -> pinned host u every "
-                          "step; uploads and downloads on their own streams overlapping neighbouring solves",
+                "method": "fem_fft_solve_host (C ABI, host buffers): pinned host b -> device, solve, device -> "
+                          "pinned host u every step; the library pipelines uploads and downloads on its own "
+                          "streams under neighbouring solves",
                 "serial": {"value": job_value(dof, ws, ms_e2e_serial), "ms_per_step": ms_e2e_serial}},
         "roofline": roof,
         "kernels": kernels,

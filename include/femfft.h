@@ -205,6 +205,27 @@ int fem_fft_set_algorithm(fem_fft_plan plan, int algo, void* stream);
  */
 int fem_fft_plan_tune(fem_fft_plan plan, void* stream);
 
+/*
+ * fem_fft_solve_host -- u = L^{-1} b for right-hand sides in HOST memory
+ * (the solve of fem_fft_solve, Section 4), with the copies pipelined inside
+ * the library: two device slots of max_nrhs fields (allocated at the first
+ * call, owned by the plan) alternate between successive calls (and groups of
+ * max_nrhs right-hand sides), and the upload of one and the download of the
+ * one before run on the plan's own copy streams under the solve of the
+ * current one.  No paper counterpart (a serving path).
+ *   h_b  [nrhs][M..] float64 host memory, read by the upload; it must hold
+ *        the data when the call is made and stay unchanged until the upload
+ *        has run (use pinned memory for asynchronous, overlapped copies)
+ *   h_u  [nrhs][M..] float64 host memory, written by the download
+ *   stream  work on it before the call precedes the uploads; h_u is complete
+ *        once the stream has passed fem_fft_host_wait(plan, stream)
+ * Asynchronous.  Other calls on the plan must not run between a host solve
+ * and the wait that completes it (they share the plan's workspace).
+ * fem_fft_host_wait -- make `stream` wait for every download issued so far.
+ */
+int fem_fft_solve_host(fem_fft_plan plan, const double* h_b, double* h_u, int64_t nrhs, void* stream);
+int fem_fft_host_wait(fem_fft_plan plan, void* stream);
+
 /* Refinement controls of the MIXED precision (ignored in FP64). */
 int fem_fft_set_refinement(fem_fft_plan plan, double rtol, int max_iter);
 

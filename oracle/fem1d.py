@@ -369,6 +369,14 @@ def theorem1_basis(n, K, dps=40):
     return lam, S, cnorm2
 
 
+def _sinpi_ratio(m, K):
+    """sin(pi m / K) for integer arrays m: the argument is reduced exactly in
+    integers (m mod 2K) before the float64 sine, so its error does not grow
+    with m (pi m / K reaches ~10^4 for the long pencils of Section 5)."""
+    r = np.mod(np.asarray(m, dtype=np.int64), 2 * K)
+    return np.sin(np.pi * r / K)
+
+
 def _theorem1_vector(n, K, k, p):
     """s_k in the fine-grid ordering for a given p (Section 3, Theorem 1,
     item 3): node j (1..K-1) -> sin(pi k j / K); interior of element j
@@ -376,8 +384,8 @@ def _theorem1_vector(n, K, k, p):
     M = dof_count(n, K)
     s = np.zeros(M)
     j = np.arange(1, K + 1)
-    sl = np.sin(np.pi * k * (j - 1) / K)          # sin at the element's left node
-    sr = np.sin(np.pi * k * j / K)                # sin at the element's right node
+    sl = _sinpi_ratio(k * (j - 1), K)             # sin(pi k (j-1) / K) at the element's left node
+    sr = _sinpi_ratio(k * j, K)                   # sin(pi k j / K) at the element's right node
     blocks = np.zeros((K, n))
     if n > 1:
         blocks[:, :n - 1] = np.outer(sl, p) + np.outer(sr, flip(p))

@@ -155,6 +155,31 @@ class Plan:
                    "fem_fft_forward")
         return c
 
+    def solve_host(self, b_host, u_host, stream=None):
+        """u_host = L^-1 b_host for float64 CPU tensors (pinned for overlap),
+        through fem_fft_solve_host: the copies are pipelined with the solves
+        of neighbouring calls inside the library.  Asynchronous: call
+        ``host_wait`` (then synchronise the stream) before reading u_host."""
+        torch = _torch()
+        for x, nm in ((b_host, "b_host"), (u_host, "u_host")):
+            if not isinstance(x, torch.Tensor) or x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+                raise TypeError(f"{nm} must be a contiguous float64 CPU tensor")
+        if tuple(b_host.shape) == self.M:
+            nrhs = 1
+        elif b_host.dim() == self.N + 1 and tuple(b_host.shape[1:]) == self.M:
+            nrhs = b_host.shape[0]
+        else:
+            raise ValueError("b_host has the wrong shape")
+        if u_host.shape != b_host.shape:
+            raise ValueError("u_host shape mismatch")
+        _lib.check(_lib.lib().fem_fft_solve_host(self._h, b_host.data_ptr(), u_host.data_ptr(), nrhs,
+                                                 self._stream(stream)), "fem_fft_solve_host")
+        return u_host
+
+    def host_wait(self, stream=None):
+        """Make the stream wait for every download of ``solve_host``."""
+        _lib.check(_lib.lib().fem_fft_host_wait(self._h, self._stream(stream)), "fem_fft_host_wait")
+
     def forward_fn(self, w, out=None, stream=None):
         """Direct F_n coefficients along every axis (float64; the mass product
         folded into the forward maps, Theorem 2 item 3)."""
@@ -402,73 +427,33 @@ class HeatStepper:
 
 
 class HostSolveStream:
-    """Solves of right-hand sides held in pinned host memory, pipelined: the
-    upload of a right-hand side and the download of a solution run on their
-    own CUDA streams while other solves run on the compute stream, over
-    ``depth`` device buffer pairs.  ``submit(b_host, u_host)`` queues
-    b -> device, u = L^-1 b (``Plan.solve``), u -> u_host and returns at once;
-    ``wait()`` makes the compute stream wait for every queued download, and
+    """Solves of right-hand sides held in (pinned) host memory through the
+    library's pipelined host-buffer path (fem_fft_solve_host): the upload of a
+    right-hand side and the download of a solution run on the plan's copy
+    streams under the neighbouring solves, over two device slots the plan
+    owns.  ``submit(b_host, u_host)`` queues one solve and returns at once;
+    ``wait()`` makes the stream wait for every queued download and
     ``synchronize()`` waits on the host.  Host tensors must stay alive and
-    unmodified until their transfer has completed (pinned float64 tensors of
-    the plan's field shape, or (nrhs,) + that shape)."""
+    unmodified until their transfer has completed (float64 CPU tensors of the
+    plan's field shape, or (nrhs,) + that shape)."""
 
-    def __init__(self, plan, nrhs=1, depth=2):
-        torch = _torch()
-        if depth < 1:
-            raise ValueError("depth must be >= 1")
+    def __init__(self, plan, nrhs=1):
         self.plan = plan
-        shape = plan.M if nrhs == 1 else (int(nrhs),) + tuple(plan.M)
-        dev = plan._torch_device
-        self._b = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(depth)]
-        self._u = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(depth)]
-        self._h2d = torch.cuda.Stream(device=dev)
-        self._d2h = torch.cuda.Stream(device=dev)
-        self._solved = [None] * depth   # solve that last read b[i] and wrote u[i]
-        self._down = [None] * depth     # download that last read u[i]
-        self._k = 0
+        self.shape = tuple(plan.M) if nrhs == 1 else (int(nrhs),) + tuple(plan.M)
 
     def submit(self, b_host, u_host, stream=None):
-        torch = _torch()
-        comp = stream if stream is not None else torch.cuda.current_stream()
-        i = self._k % len(self._b)
-        if b_host.shape != self._b[i].shape or u_host.shape != self._u[i].shape:
+        if tuple(b_host.shape) != self.shape or tuple(u_host.shape) != self.shape:
             raise ValueError("host tensors must have the stream's field shape")
-        up = torch.cuda.Event()
-        with torch.cuda.stream(self._h2d):
-            if self._solved[i] is not None:
-                self._h2d.wait_event(self._solved[i])   # b[i] is no longer read
-            self._b[i].copy_(b_host, non_blocking=True)
-            up.record(self._h2d)
-        comp.wait_event(up)
-        if self._down[i] is not None:
-            comp.wait_event(self._down[i])              # u[i] has been read back
-        self.plan.solve(self._b[i], out=self._u[i], stream=comp)
-        solved = torch.cuda.Event()
-        solved.record(comp)
-        self._solved[i] = solved
-        down = torch.cuda.Event()
-        with torch.cuda.stream(self._d2h):
-            self._d2h.wait_event(solved)
-            u_host.copy_(self._u[i], non_blocking=True)
-            down.record(self._d2h)
-        self._down[i] = down
-        self._k += 1
-
-    def start_after(self, event):
-        """Later uploads wait for ``event`` (e.g. the start of a timed region)."""
-        self._h2d.wait_event(event)
+        self.plan.solve_host(b_host, u_host, stream=stream)
 
     def wait(self, stream=None):
-        torch = _torch()
-        comp = stream if stream is not None else torch.cuda.current_stream()
-        for ev in self._down:
-            if ev is not None:
-                comp.wait_event(ev)
+        self.plan.host_wait(stream=stream)
 
-    def synchronize(self):
-        for ev in self._down:
-            if ev is not None:
-                ev.synchronize()
+    def synchronize(self, stream=None):
+        torch = _torch()
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.plan.host_wait(stream=st)
+        st.synchronize()
 
 
 def batch_order(nsteps, work=None):

@@ -54,6 +54,8 @@ def lib():
         "fem_fft_last_info": ([vp, PI, PD], i32),
         "fem_fft_forward": ([vp, vp, vp, i64, vp], i32),
         "fem_fft_forward_fn": ([vp, vp, vp, i64, vp], i32),
+        "fem_fft_solve_host": ([vp, vp, vp, i64, vp], i32),
+        "fem_fft_host_wait": ([vp, vp], i32),
         "fem_fft_heat_step": ([vp, f64, vp, vp, vp, i64, vp], i32),
         "fem_fft_inverse": ([vp, vp, vp, i64, vp], i32),
         "fem_fft_grad_coeffs": ([vp, vp, vp, i64, PD, PD, vp], i32),

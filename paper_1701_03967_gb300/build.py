@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libfemfft.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["pencil_f64.cu", "pencil_f32.cu", "pencil_fast_f32_v16.cu", "pencil_fast_f32_v32.cu", "apply.cu",
               "api.cu", "noalloc.cu", "batch.cu", "batch_k1.cu", "batch_k2.cu", "batch_k3.cu", "band.cu",
-              "dirichlet.cu"]
+              "dirichlet.cu", "host.cu", "longpass.cu"]
 CPP_SOURCES = ["precompute.cpp", "pencil_fast_plan.cpp"]
 
 

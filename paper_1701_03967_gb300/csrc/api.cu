@@ -323,9 +323,19 @@ struct FastPlan {
   int threads;
 };
 
-bool fast_eligible(fem_fft_plan p, int mode, int axis, bool f64) {
+bool fast_possible(fem_fft_plan p, int mode, int axis, bool f64) {
   return p->fast_passes && !f64 && !p->rec && p->ax[axis].fast_V && p->t32[axis].gmap &&
          (mode == MODE_FWD || mode == MODE_INV || mode == MODE_FUSED);
+}
+
+// The register-radix kernels where they apply and were measured faster
+// (fem_fft_plan_tune), else by default for K >= 512: on the short pencils of
+// the 3D and batched workloads (K <= 128) the shared-memory Stockham kernels,
+// at two CTAs per SM, measured faster.
+bool fast_eligible(fem_fft_plan p, int mode, int axis, bool f64) {
+  if (!fast_possible(p, mode, axis, f64)) return false;
+  const int ch = p->fast_choice[mode][axis];
+  return ch < 0 ? p->K[axis] >= 512 : ch == 1;
 }
 
 int plan_fast(fem_fft_plan p, int mode, int axis, long long outer, long long inner, int Wwant, FastPlan* fp) {
@@ -432,6 +442,15 @@ int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const
     return run_fast(p, mode, axis, outer, inner, in, in_f64, out, out_f64, accum, s);
   PassPlan pp;
   int rc = plan_pass(p, mode, axis, outer, inner, f64, &pp);
+  if (rc == FEM_FFT_ERR_ARG && inner == 1 && !p->rec && (mode != MODE_FUSED || p->N == 1)) {
+    // a contiguous pencil too long for one CTA: the global four-step path
+    const double elems = (double)outer * p->M[axis];
+    const double bytes = elems * ((in_f64 ? 8 : 4) + (out_f64 ? 8 : 4) * (accum ? 2 : 1));
+    const int kind = mode == MODE_FWD ? 0 : (mode == MODE_FUSED ? 1 : 2);
+    ProfScope scope(p, s, kind, bytes, 0.0);
+    return run_long_pass(p, mode, axis, outer, in, in_f64, out, out_f64, accum, f64,
+                         (in_f64 && in == p->check_in) ? p->d_flag : nullptr, s);
+  }
   if (rc) return rc;
   PassParams& P = pp.P;
   P.in = in;
@@ -1130,8 +1149,17 @@ int fem_fft_plan_destroy(fem_fft_plan p) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+  if (p->long_ws) cudaFree(p->long_ws);
   if (p->h_flag) cudaFreeHost(p->h_flag);
   if (p->flag_ev) cudaEventDestroy(p->flag_ev);
+  for (int i = 0; i < 2; ++i) {
+    if (p->hs_ev_in[i]) cudaEventDestroy(p->hs_ev_in[i]);
+    if (p->hs_ev_solved[i]) cudaEventDestroy(p->hs_ev_solved[i]);
+    if (p->hs_ev_out[i]) cudaEventDestroy(p->hs_ev_out[i]);
+  }
+  if (p->hs_ev_entry) cudaEventDestroy(p->hs_ev_entry);
+  for (int i = 0; i < 3; ++i)
+    if (p->hs_stream[i]) cudaStreamDestroy(p->hs_stream[i]);
   delete p;
   return FEM_FFT_OK;
 }
@@ -1506,7 +1534,9 @@ int fem_fft_plan_tune(fem_fft_plan p, void* stream) {
   passes.push_back({MODE_FUSED, 0});
   for (int ax = 1; ax < p->N; ++ax) passes.push_back({MODE_INV, ax});
   for (const Pass& ps : passes) {
-    if (fast_eligible(p, ps.mode, ps.axis, f64)) {
+    float fast_best_ms = 1e30f;
+    if (fast_possible(p, ps.mode, ps.axis, f64)) {
+      p->fast_choice[ps.mode][ps.axis] = 1;
       // register-radix pass: pencils per tile W in 1, 2, 4, ... (the radix
       // schedule is fixed by K)
       int bestW = 0;
@@ -1534,8 +1564,9 @@ int fem_fft_plan_tune(fem_fft_plan p, void* stream) {
         }
       }
       p->fast_W[ps.mode][ps.axis] = bestW;   // 0: the heuristic
+      fast_best_ms = best_ms;
       if (rc) break;
-      continue;
+      p->fast_choice[ps.mode][ps.axis] = 0;   // now time the shared-memory kernels
     }
     fem_fft_plan_s::Tuned& tu = p->tuned[ps.mode][ps.axis][f64 ? 1 : 0];
     const int K = (int)p->K[ps.axis];
@@ -1573,6 +1604,8 @@ int fem_fft_plan_tune(fem_fft_plan p, void* stream) {
       if (rc) break;
     }
     tu = best;   // W = 0 (heuristic) if no candidate ran
+    if (fast_possible(p, ps.mode, ps.axis, f64))
+      p->fast_choice[ps.mode][ps.axis] = fast_best_ms <= best_ms ? 1 : 0;
     if (rc) break;
   }
   p->profiling = was_profiling;

@@ -71,6 +71,11 @@ int tile_pitch(int K, int Q, int V, int W, bool strided, int elem_bytes);
 // Records the mixed-precision solve of nrhs right-hand sides (b -> u, then
 // `steps` refinement steps) as the plan would launch it.  nrhs must not
 // exceed the plan's max_nrhs.  b and u may be placeholder addresses.
+// A pencil pass over contiguous pencils too long for one CTA's shared memory
+// (longpass.cu): global-memory four-step FFT path.  f64: the pass's arithmetic.
+int run_long_pass(fem_fft_plan p, int mode, int axis, long long outer, const void* in, bool in_f64, void* out,
+                  bool out_f64, bool accum, bool f64, int* nonfinite, cudaStream_t s);
+
 int record_mixed_solve(fem_fft_plan p, const double* b, double* u, long long nrhs, int steps,
                        std::vector<RecordedOp>* ops);
 
@@ -104,9 +109,14 @@ struct fem_fft_plan_s {
     int W = 0, V = 0;
   };
   Tuned tuned[3][femfft::kMaxN][2];
-  // float passes on the register-radix kernels where the axis allows it
-  // (fem_fft_set_pass_kernels); pencils per tile chosen by fem_fft_plan_tune
+  // float passes on the register-radix kernels (pencil_fast.cuh) where the
+  // axis allows it; fem_fft_plan_tune picks, per [mode][axis], the faster of
+  // them and the shared-memory Stockham kernels (fast_choice: -1 not tuned,
+  // which means the register-radix kernels for K >= 512; 0 / 1) and their
+  // pencils per tile (fast_W, 0: the heuristic)
   int fast_passes = 1;
+  int fast_W[3][femfft::kMaxN] = {{0}};
+  int fast_choice[3][femfft::kMaxN] = {{-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}};
   // forward passes read the direct F_n-transform maps (fem_fft_forward_fn)
   int use_fwdc = 0;
   // non-finite input detection: the first pass of a solve that reads the
@@ -117,7 +127,17 @@ struct fem_fft_plan_s {
   cudaEvent_t flag_ev = nullptr;
   const void* check_in = nullptr;
   int last_status = 0;                 // FEM_FFT_OK or FEM_FFT_ERR_NOT_CONVERGED of the last solve
-  int fast_W[3][femfft::kMaxN] = {{0}};
+  // host-buffer solves (host.cu): two device slots, three streams
+  int hs_ready = 0;
+  long long hs_calls = 0;
+  double* hs_b[2] = {nullptr, nullptr};
+  double* hs_u[2] = {nullptr, nullptr};
+  cudaEvent_t hs_ev_in[2] = {nullptr, nullptr}, hs_ev_solved[2] = {nullptr, nullptr},
+              hs_ev_out[2] = {nullptr, nullptr}, hs_ev_entry = nullptr;
+  cudaStream_t hs_stream[3] = {nullptr, nullptr, nullptr};
+  // long contiguous pencils (longpass.cu): workspace of packed sequences
+  void* long_ws = nullptr;
+  size_t long_ws_bytes = 0;
   // algorithm (b) of Section 4 (fem_fft_set_algorithm): band-solve tables
   // per position of the later axes (float64 and float32 copies), the element
   // data and the vertex-solve scratch

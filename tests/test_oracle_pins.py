@@ -406,3 +406,30 @@ def test_dirichlet_data_reproduce_polynomials(case):
     assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
     # without the correction the boundary values are lost
     assert np.max(np.abs(solve.solve(prob, b) - want)) > 1e-3 * np.max(np.abs(want))
+
+
+def test_basis_node_values_exact_at_long_pencils():
+    """Theorem 1, item 3: the node values of s_k^(l) are sin(pi k j / K).
+    At the long pencils of Section 5 (pi k j / K up to ~10^4) the oracle's
+    basis must keep them to float64 rounding (exact argument reduction),
+    checked against 40-digit values; and its interior values against the
+    formula p sin(pi k (j-1)/K) + p^ sin(pi k j / K) at 40 digits."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    n, K = 2, 4096
+    lam, S, cn = fem1d.theorem1_basis(n, K)
+    rng = np.random.default_rng(3)
+    # columns of S: bubble modes first, then k = 1..K-1 with n modes each
+    for col in rng.choice(np.arange(n - 1, S.shape[1]), 12, replace=False):
+        k = (col + 1) // n
+        for j in rng.choice(np.arange(1, K), 12, replace=False):
+            node = n * j - 1                     # fine index of node j
+            want = float(mp.sin(mp.pi * k * j / K))
+            assert abs(S[node, col] - want) <= 2e-15, (col, j)   # pi m / K reduced below 2 pi
+        # interior of element j: p sin(pi k (j-1)/K) + p^ sin(pi k j/K), p = S[interior of element 1]
+        p = S[0:n - 1, col] / max(1e-300, float(mp.sin(mp.pi * k / K)))   # element 1: p^ sin(pi k / K)
+        for j in rng.choice(np.arange(1, K + 1), 6, replace=False):
+            want = [float(p[n - 2 - i] * mp.sin(mp.pi * k * (j - 1) / K) + p[i] * mp.sin(mp.pi * k * j / K))
+                    for i in range(n - 1)]
+            got = S[n * (j - 1): n * (j - 1) + n - 1, col]
+            assert np.max(np.abs(got - np.array(want)[::-1])) <= 1e-12 * max(1.0, np.max(np.abs(want)))
