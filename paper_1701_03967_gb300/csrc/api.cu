@@ -345,7 +345,10 @@ int plan_fast(fem_fft_plan p, int mode, int axis, long long outer, long long inn
   FastParams& P = fp->P;
   std::memset(&P, 0, sizeof(P));
   const size_t csize = 2 * sizeof(float);
-  const size_t budget = (size_t)std::min(p->smem_optin, 220 * 1024);
+  // shared memory per CTA: the kernels compiled for two CTAs per SM get half
+  const int ctas = (ax.fast_V == 32 && mode != MODE_FUSED) ? 2 : 1;
+  const size_t budget = ctas == 2 ? (size_t)std::min(p->smem_optin, 112 * 1024)
+                                  : (size_t)std::min(p->smem_optin, 220 * 1024);
   long long wmax = (long long)(budget / ((size_t)(K * Qp + 16) * csize));
   wmax = std::min<long long>(wmax, std::min<long long>(kMaxW, (long long)kFastChunkTasks * threads / K));
   if (wmax < 1) return FEM_FFT_ERR_ARG;
@@ -389,13 +392,29 @@ int plan_fast(fem_fft_plan p, int mode, int axis, long long outer, long long inn
     P.twofs[s] = ax.fast_twofs[s];
   }
   fast_layout(K, Q, Qp, (int)W, P.V, P.npass, P.radix, threads, &P.seq_order, &P.pitch, P.swz);
+  if ((size_t)W * P.pitch * csize > budget) {   // the pitch slack of the bank model
+    W = std::max<long long>(1, W - 1);
+    if (inner > 1) {
+      long long p2 = 1;
+      while (p2 * 2 <= W) p2 *= 2;
+      W = p2;
+    }
+    P.g.W = (int)W;
+    if (inner == 1) {
+      P.g.tiles_inner = 1;
+      P.g.tiles = (outer + W - 1) / W;
+    } else {
+      P.g.tiles_inner = (inner + W - 1) / W;
+      P.g.tiles = outer * P.g.tiles_inner;
+    }
+    fast_layout(K, Q, Qp, (int)W, P.V, P.npass, P.radix, threads, &P.seq_order, &P.pitch, P.swz);
+  }
   const DevTables& d = p->t32[axis];
   P.tw2 = d.tw2;
   P.rot = d.rot;
   P.gmap = d.gmap;
   P.invn = d.invn;
   P.muk = d.muk;
-  (void)mode;
   fp->smem = (size_t)W * P.pitch * csize;
   fp->threads = threads;
   return FEM_FFT_OK;

@@ -71,8 +71,10 @@ template <typename T>
 __device__ __forceinline__ T load_in(const LongParams& P, long long idx, bool& nf) {
   if (P.in_f64) {
     const double x = reinterpret_cast<const double*>(P.in)[idx];
-    if (P.nonfinite) nf |= !isfinite(x);
-    return T(x);
+    if (P.nonfinite) nf |= nonfinite_f64(x);
+    T v;
+    from_f64(x, v);
+    return v;
   }
   return T(reinterpret_cast<const float*>(P.in)[idx]);
 }
@@ -81,7 +83,7 @@ template <typename T>
 __device__ __forceinline__ void store_out(const LongParams& P, long long idx, T v) {
   if (P.out_f64) {
     double* o = reinterpret_cast<double*>(P.out) + idx;
-    *o = P.accum ? *o + double(v) : double(v);
+    *o = P.accum ? *o + to_f64(v) : to_f64(v);
   } else {
     float* o = reinterpret_cast<float*>(P.out) + idx;
     *o = P.accum ? *o + float(v) : float(v);

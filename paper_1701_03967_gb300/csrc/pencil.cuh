@@ -69,6 +69,49 @@ __device__ __forceinline__ cpx<T> ld_cpx(const void* base, int idx) {
   return {__ldg(p), __ldg(p + 1)};
 }
 
+// float64 <-> float32 by integer bit operations.  GB300 issues about two
+// float64 operations per clock per SM, so the conversions at the float64
+// inputs and outputs of the float32 passes (and the non-finite test) would
+// otherwise take a sizeable share of those passes on the float64 pipe.
+// f64_to_f32_bits: round to nearest even; |x| < 2^-126 flushes to a signed
+// zero, |x| >= 2^128 (after rounding) gives infinity, NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_int(long long xbits) {
+  // branch-free (selects only), so that the loads around it stay in flight
+  const unsigned long long b = (unsigned long long)xbits;
+  const unsigned hi = (unsigned)(b >> 32);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned long long m = b & 0x000fffffffffffffull;
+  const int fe = e - 1023 + 127;
+  unsigned r = ((unsigned)(fe & 0xff) << 23) | (unsigned)(m >> 29);
+  const unsigned rem = (unsigned)(m & 0x1fffffffu);
+  r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;   // a carry may reach infinity
+  r = fe >= 255 ? 0x7f800000u : r;
+  r = fe <= 0 ? 0u : r;
+  r = e == 0x7ff ? (0x7f800000u | (m ? 0x00400000u : 0u)) : r;
+  return __uint_as_float(sign | r);
+}
+// the exact float64 value of a float (subnormal floats flush to zero)
+__device__ __forceinline__ double f32_to_f64_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long s = (unsigned long long)(u >> 31) << 63;
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  if (e == 0) return __longlong_as_double((long long)s);
+  const unsigned long long de = e == 255 ? 0x7ffull : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(s | (de << 52) | m));
+}
+__device__ __forceinline__ bool f64_nonfinite_int(long long xbits) {
+  return ((((unsigned long long)xbits) >> 52) & 0x7ffu) == 0x7ffu;
+}
+// a float64 field value as T: float by the integer conversion, double as is
+__device__ __forceinline__ void from_f64(double x, float& out) { out = f64_to_f32_int(__double_as_longlong(x)); }
+__device__ __forceinline__ void from_f64(double x, double& out) { out = x; }
+__device__ __forceinline__ bool nonfinite_f64(double x) { return f64_nonfinite_int(__double_as_longlong(x)); }
+// T as float64: exact for both
+__device__ __forceinline__ double to_f64(float v) { return f32_to_f64_int(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+
 // MODE_FWD_DIV: the forward transform with the spectral division, stored in
 // spectral order (the fused pass split in two; used by the batched kernel).
 enum PassMode { MODE_FWD = 0, MODE_INV = 1, MODE_FUSED = 2, MODE_FWD_DIV = 3 };
@@ -317,31 +360,45 @@ __device__ bool load_tile(T* smr, const PassParams& P, long long tile, bool spec
   const PassGeom& g = P.g;
   const int M = g.M;
   const int sh = spectral ? 1 : 0;
+  const double* ind = reinterpret_cast<const double*>(P.in);
+  const float* inf = reinterpret_cast<const float*>(P.in);
+  // one batch of kLoadBatch values: all loads issued first, then converted
+  // and stored (a conversion between the loads would hold the later ones back)
+  auto batch = [&](T* dst, int i0, int istep, long long base, long long stride) {
+    if (P.in_f64) {
+      double x[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int i = i0 + u * istep;
+        x[u] = (i < M && base >= 0) ? ld_field<NC>(ind + base + (long long)i * stride) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int i = i0 + u * istep;
+        if (check) nf |= nonfinite_f64(x[u]);
+        T v;
+        from_f64(x[u], v);
+        if (i < M) dst[chunk_slot<NORD, Q2>(i + sh)] = v;
+      }
+    } else {
+      float x[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int i = i0 + u * istep;
+        x[u] = (i < M && base >= 0) ? ld_field<NC>(inf + base + (long long)i * stride) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int i = i0 + u * istep;
+        if (i < M) dst[chunk_slot<NORD, Q2>(i + sh)] = T(x[u]);
+      }
+    }
+  };
   if (g.inner == 1) {
     for (int p = 0; p < g.W; ++p) {
       const long long base = pencil_base(g, tile, p);
       T* dst = smr + 2 * p * P.pitch;
-      for (int i0 = threadIdx.x; i0 < M; i0 += kLoadBatch * blockDim.x) {
-        T v[kLoadBatch];
-#pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-          const int i = i0 + u * blockDim.x;
-          v[u] = T(0);
-          if (i < M && base >= 0) {
-            if (P.in_f64) {
-              const double x = ld_field<NC>(reinterpret_cast<const double*>(P.in) + base + i);
-              if (check) nf |= !isfinite(x);
-              v[u] = T(x);
-            }
-            else v[u] = T(ld_field<NC>(reinterpret_cast<const float*>(P.in) + base + i));
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kLoadBatch; ++u) {
-          const int i = i0 + u * blockDim.x;
-          if (i < M) dst[chunk_slot<NORD, Q2>(i + sh)] = v[u];
-        }
-      }
+      for (int i0 = threadIdx.x; i0 < M; i0 += kLoadBatch * blockDim.x) batch(dst, i0, blockDim.x, base, 1);
     }
     return nf;
   }
@@ -349,30 +406,8 @@ __device__ bool load_tile(T* smr, const PassParams& P, long long tile, bool spec
   const int p = threadIdx.x & (W - 1);
   const int istep = blockDim.x / W;
   const long long base = pencil_base(g, tile, p);
-  const long long stride = g.inner;
   T* dst = smr + 2 * p * P.pitch;
-  for (int i0 = threadIdx.x / W; i0 < M; i0 += kLoadBatch * istep) {
-    T v[kLoadBatch];
-#pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
-      const int i = i0 + u * istep;
-      v[u] = T(0);
-      if (i < M && base >= 0) {
-        const long long off = base + (long long)i * stride;
-        if (P.in_f64) {
-          const double x = ld_field<NC>(reinterpret_cast<const double*>(P.in) + off);
-          if (check) nf |= !isfinite(x);
-          v[u] = T(x);
-        }
-        else v[u] = T(ld_field<NC>(reinterpret_cast<const float*>(P.in) + off));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
-      const int i = i0 + u * istep;
-      if (i < M) dst[chunk_slot<NORD, Q2>(i + sh)] = v[u];
-    }
-  }
+  for (int i0 = threadIdx.x / W; i0 < M; i0 += kLoadBatch * istep) batch(dst, i0, istep, base, g.inner);
   return nf;
 }
 
@@ -380,7 +415,7 @@ template <typename T, bool NC>
 __device__ __forceinline__ void store_one(const PassParams& P, long long off, T v) {
   if (P.out_f64) {
     double* o = reinterpret_cast<double*>(P.out) + off;
-    *o = P.accum ? (NC ? *o : __ldcg(o)) + double(v) : double(v);
+    *o = P.accum ? (NC ? *o : __ldcg(o)) + to_f64(v) : to_f64(v);
   } else {
     float* o = reinterpret_cast<float*>(P.out) + off;
     *o = P.accum ? (NC ? *o : __ldcg(o)) + float(v) : float(v);

@@ -46,6 +46,14 @@ namespace femfft {
 // thread (at 128 registers ptxas spills)
 template <int V>
 __host__ __device__ constexpr int fast_threads() { return V == 32 ? 320 : 512; }
+// resident CTAs per SM the kernels are compiled for: two for the forward and
+// inverse passes of the V = 32 schedules (96 registers per thread, a few
+// hundred bytes of spills, but the load/store phase of one CTA overlaps the
+// FFT and map phases of the other: measured 1.04 -> 0.69 ms (forward) and
+// 0.99 -> 0.78 ms (inverse) per 2D n = 9 K = 1024 launch); one for the fused
+// pass (strided pencils, 0.85 -> 1.13 ms at two) and for V = 16
+template <int V, int MODE>
+__host__ __device__ constexpr int fast_min_blocks() { return (V == 32 && MODE != 2) ? 2 : 1; }
 // chunks per thread of the sequence build (W K <= kFastChunkTasks threads)
 constexpr int kFastChunkTasks = 16;
 
@@ -350,20 +358,20 @@ __device__ bool fast_load(T* smr, const FastParams& P, long long tile, bool spec
         continue;
       }
       for (int i0 = threadIdx.x; i0 < M; i0 += LB * blockDim.x) {
-        T v[LB];
+        // every load of the batch is issued before any value is converted
+        double x[LB];
 #pragma unroll
         for (int u = 0; u < LB; ++u) {
           const int i = i0 + u * blockDim.x;
-          if (i < M) {
-            const double x = ld_field<NC>(ind + base + i);
-            if (check) nf |= !isfinite(x);
-            v[u] = T(x);
-          }
+          x[u] = i < M ? ld_field<NC>(ind + base + i) : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < LB; ++u) {
           const int i = i0 + u * blockDim.x;
-          if (i < M) dst[fast_slot<NORD, Q2p>(i + sh)] = v[u];
+          if (check) nf |= nonfinite_f64(x[u]);
+          T v;
+          from_f64(x[u], v);
+          if (i < M) dst[fast_slot<NORD, Q2p>(i + sh)] = v;
         }
       }
     }
@@ -384,20 +392,19 @@ __device__ bool fast_load(T* smr, const FastParams& P, long long tile, bool spec
     return nf;
   }
   for (int i0 = threadIdx.x / W; i0 < M; i0 += LB * istep) {
-    T v[LB];
+    double x[LB];
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
       const int i = i0 + u * istep;
-      if (i < M) {
-        const double x = ld_field<NC>(ind + base + (long long)i * stride);
-        if (check) nf |= !isfinite(x);
-        v[u] = T(x);
-      }
+      x[u] = i < M ? ld_field<NC>(ind + base + (long long)i * stride) : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < LB; ++u) {
       const int i = i0 + u * istep;
-      if (i < M) dst[fast_slot<NORD, Q2p>(i + sh)] = v[u];
+      if (check) nf |= nonfinite_f64(x[u]);
+      T v;
+      from_f64(x[u], v);
+      if (i < M) dst[fast_slot<NORD, Q2p>(i + sh)] = v;
     }
   }
   return nf;
@@ -436,7 +443,10 @@ __device__ void fast_store(const T* smr, const FastParams& P, long long tile, bo
 #pragma unroll
         for (int u = 0; u < SB; ++u) {
           const int i = i0 + u * istep;
-          if (i < M) o[(long long)i * stride] = old[u] + double(src[fast_slot<NORD, Q2p>(i + sh)]);
+          if (i < M) {
+            const double v = to_f64(src[fast_slot<NORD, Q2p>(i + sh)]);
+            o[(long long)i * stride] = P.accum ? old[u] + v : v;   // one float64 add when accumulating
+          }
         }
       }
     } else {
@@ -814,7 +824,7 @@ __device__ __forceinline__ void fast_tile(const FastParams& P, long long tile, u
 // so that those loads do not wait on HBM latency.  (A persistent loop over
 // tiles would do the same but made ptxas spill heavily.)
 template <typename T, int NORD, int MODE, int V>
-__global__ void __launch_bounds__(fast_threads<V>(), 1) pencil_fast_kernel(FastParams P) {
+__global__ void __launch_bounds__(fast_threads<V>(), (fast_min_blocks<V, MODE>())) pencil_fast_kernel(FastParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T den_base[kMaxW];
   const long long tile = blockIdx.x;

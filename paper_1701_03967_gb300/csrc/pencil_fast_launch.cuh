@@ -10,14 +10,14 @@ static int launch_fast_one(const FastParams& P, size_t smem, int threads, cudaSt
   auto kern = pencil_fast_kernel<T, NORD, MODE, V>;
   const int e = ensure_dyn_smem((const void*)kern, smem);
   if (e) return e;
-  // one CTA per SM at a time: the prefetch distance is the SM count
+  // the prefetch distance: the CTAs resident at a time
   static int sms[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   int& nsm = sms[dev >= 0 && dev < 64 ? dev : 0];
   if (!nsm && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm = 0;
   FastParams Pl = P;
-  Pl.ahead = nsm;
+  Pl.ahead = nsm * fast_min_blocks<V, MODE>();   // the CTAs resident at a time
   kern<<<(unsigned)P.g.tiles, threads, smem, s>>>(Pl);
   return (int)cudaGetLastError();
 }
