@@ -480,6 +480,48 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+PROFILE_CASES = {
+    # name: (precision, n, K, X, a, c, algorithm); small cases for kernel captures (fields above L2,
+    # at most about 1 GB on the device)
+    "fast2d": ("mixed", 9, (1024, 1024), (1.0, 2.0), (1.0, 2.5), 1.0, "a"),
+    "mid2d": ("mixed", 9, (512, 512), (1.0, 2.0), (1.0, 2.5), 1.0, "a"),
+    "f64_2d": ("fp64", 9, (512, 512), (1.0, 2.0), (1.0, 2.5), 1.0, "a"),
+    "band2d": ("mixed", 9, (512, 512), (1.0, 2.0), (1.0, 2.5), 1.0, "b"),
+    "fast3d": ("mixed", 5, (64, 64, 64), (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), 0.0, "a"),
+    "long1d": ("mixed", 5, (1 << 20,), (1.0,), (1.0,), 0.0, "a"),
+}
+
+
+def run_profile_case(case):
+    """Two solves of a small case and nothing else (no timing): the program an ncu capture of
+    one kernel runs.  "batch": 24 problems of the batched workload in one batch."""
+    import torch
+    from paper_1701_03967_gb300 import Batch, Plan, synth
+    dev = "cuda"
+    if case == "batch":
+        specs = synth.batched_problems()[:24]
+        plans = [Plan(s["n"], s["K"], s["X"], s["a"], s["c"], "mixed", max_nrhs=s["nrhs"]) for s in specs]
+        bt = Batch(plans, [s["nrhs"] for s in specs], tune=False)
+        x = torch.from_numpy(synth.normal_field((bt.total_len,), synth.CFG_TEST, 0, 0)).to(dev)
+        u = torch.empty_like(x)
+        for _ in range(2):
+            bt.solve(x, out=u)
+        bt.check()
+        torch.cuda.synchronize()
+        print("ok batch", bt.total_len)
+        return
+    prec, n, K, X, a, c, algo = PROFILE_CASES[case]
+    pl = Plan(n, K, X, a, c, precision=prec)
+    if algo == "b":
+        pl.set_algorithm("b")
+    b = torch.from_numpy(synth.normal_field(pl.M, synth.CFG_TEST, 0, 0)).to(dev)
+    u = torch.empty_like(b)
+    for _ in range(2):
+        pl.solve(b, out=u)
+    torch.cuda.synchronize()
+    print("ok", case, float(u.norm()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -491,7 +533,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-problem batched measurement")
     ap.add_argument("--no-others", action="store_true", help="skip the n-sweep, 3D and gradient measurements")
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES) + ["batch"],
+                    help="run two solves of a small case for a kernel capture and exit (no timing, no JSON)")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     wl = WORKLOADS[args.workload]
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -464,6 +464,18 @@ int fem_fft_batch_order(int nprob, const int* nsteps, const double* work, int* h
  */
 int fem_fft_apply_tiling(int64_t inner, int64_t outer, int64_t K, int* h_tw, int64_t* h_blocks);
 
+/*
+ * fem_fft_apply_block_map -- the thread map of one block of that tiling
+ * (host only; no paper counterpart), computed by the same decode the apply
+ * kernels run: for each of the block's 256 threads t, the outer index
+ * h_o[t], the position h_w[t] (the line in lines mode) and the element h_e[t]
+ * it applies, or -1 in all three when the thread has no element.  Host
+ * arrays of 256 entries.  FEM_FFT_ERR_ARG for a non-positive size, a NULL
+ * array or a block outside [0, blocks).
+ */
+int fem_fft_apply_block_map(int64_t inner, int64_t outer, int64_t K, int64_t block, int64_t* h_o, int64_t* h_w,
+                            int64_t* h_e);
+
 /* Static text for a status code; fem_fft_last_error: the last CUDA error
  * text recorded by this thread (empty if none). */
 const char* fem_fft_strerror(int code);

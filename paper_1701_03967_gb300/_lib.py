@@ -76,6 +76,7 @@ def lib():
         "fem_fft_batch_hold_step": ([vp, i64], i32),
         "fem_fft_batch_order": ([i32, PI, PD, PI, PI], i32),
         "fem_fft_apply_tiling": ([i64, i64, i64, PI, ctypes.POINTER(ctypes.c_int64)], i32),
+        "fem_fft_apply_block_map": ([i64, i64, i64, i64, P64, P64, P64], i32),
         "fem_fft_strerror": ([i32], ctypes.c_char_p),
         "fem_fft_last_error": ([], ctypes.c_char_p),
     }

@@ -341,13 +341,13 @@ bool fast_eligible(fem_fft_plan p, int mode, int axis, bool f64) {
 int plan_fast(fem_fft_plan p, int mode, int axis, long long outer, long long inner, int Wwant, FastPlan* fp) {
   const AxisHost& ax = p->ax[axis];
   const int n = ax.n, K = ax.K, Q = n / 2 + 1, Qp = Q | 1;
-  const int threads = ax.fast_V == 32 ? fast_threads<32>() : fast_threads<16>();
+  const int threads = fast_threads_rt(ax.fast_V, mode);
   FastParams& P = fp->P;
   std::memset(&P, 0, sizeof(P));
   const size_t csize = 2 * sizeof(float);
-  // shared memory per CTA: the kernels compiled for two CTAs per SM get half
-  const int ctas = (ax.fast_V == 32 && mode != MODE_FUSED) ? 2 : 1;
-  const size_t budget = ctas == 2 ? (size_t)std::min(p->smem_optin, 112 * 1024)
+  // shared memory per CTA: the share of one of the CTAs the kernel is compiled to keep per SM
+  const int ctas = fast_ctas_rt(ax.fast_V, mode);
+  const size_t budget = ctas >= 2 ? (size_t)std::min<size_t>(p->smem_optin, 224 * 1024 / ctas)
                                   : (size_t)std::min(p->smem_optin, 220 * 1024);
   long long wmax = (long long)(budget / ((size_t)(K * Qp + 16) * csize));
   wmax = std::min<long long>(wmax, std::min<long long>(kMaxW, (long long)kFastChunkTasks * threads / K));
@@ -461,13 +461,13 @@ int run_pass(fem_fft_plan p, int mode, int axis, long long nrhs, bool f64, const
     return run_fast(p, mode, axis, outer, inner, in, in_f64, out, out_f64, accum, s);
   PassPlan pp;
   int rc = plan_pass(p, mode, axis, outer, inner, f64, &pp);
-  if (rc == FEM_FFT_ERR_ARG && inner == 1 && !p->rec && (mode != MODE_FUSED || p->N == 1)) {
-    // a contiguous pencil too long for one CTA: the global four-step path
-    const double elems = (double)outer * p->M[axis];
+  if (rc == FEM_FFT_ERR_ARG && !p->rec) {
+    // a pencil too long for one CTA: the global four-step path
+    const double elems = (double)outer * p->M[axis] * inner;
     const double bytes = elems * ((in_f64 ? 8 : 4) + (out_f64 ? 8 : 4) * (accum ? 2 : 1));
     const int kind = mode == MODE_FWD ? 0 : (mode == MODE_FUSED ? 1 : 2);
     ProfScope scope(p, s, kind, bytes, 0.0);
-    return run_long_pass(p, mode, axis, outer, in, in_f64, out, out_f64, accum, f64,
+    return run_long_pass(p, mode, axis, outer, inner, in, in_f64, out, out_f64, accum, f64,
                          (in_f64 && in == p->check_in) ? p->d_flag : nullptr, s);
   }
   if (rc) return rc;

@@ -91,3 +91,20 @@ extern "C" int fem_fft_apply_tiling(int64_t inner, int64_t outer, int64_t K, int
   if (h_blocks) *h_blocks = femfft::apply_tile_blocks(inner, outer, (int)K, TW, femfft::kApplyThreads);
   return FEM_FFT_OK;
 }
+
+extern "C" int fem_fft_apply_block_map(int64_t inner, int64_t outer, int64_t K, int64_t block, int64_t* h_o,
+                                       int64_t* h_w, int64_t* h_e) {
+  if (inner < 1 || outer < 1 || K < 1 || K > (int64_t(1) << 30) || !h_o || !h_w || !h_e) return FEM_FFT_ERR_ARG;
+  const int TW = femfft::apply_tile_w(inner, outer, (int)K, femfft::kApplyThreads);
+  if (block < 0 || block >= femfft::apply_tile_blocks(inner, outer, (int)K, TW, femfft::kApplyThreads))
+    return FEM_FFT_ERR_ARG;
+  const bool lines = inner == 1 && TW > 1;
+  for (int t = 0; t < femfft::kApplyThreads; ++t) {
+    const femfft::ApplyThread d =
+        femfft::apply_decode(block, t, TW, femfft::kApplyThreads, (int)K, inner, outer, lines);
+    h_o[t] = d.valid ? d.o : -1;
+    h_w[t] = d.valid ? d.w : -1;
+    h_e[t] = d.valid ? d.e : -1;
+  }
+  return FEM_FFT_OK;
+}

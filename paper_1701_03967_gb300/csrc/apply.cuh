@@ -214,19 +214,11 @@ __device__ __forceinline__ void apply_block(const ApplyParams& P, int TW, long l
   // lines mode (inner == 1, TW > 1): TW lines of the contiguous axis per
   // block, threads along the elements of a line (as in apply_block_df)
   const bool lines = P.inner == 1 && TW > 1;
-  const long long npos = lines ? P.outer : P.inner;
-  const long long wtiles = (npos + TW - 1) / TW;
-  const long long etiles = (K + TE - 1) / TE;
-  const long long et = bx % etiles;
-  bx /= etiles;
-  const long long wt = bx % wtiles;
-  const long long o = lines ? 0 : bx / wtiles;
-  const int tw = lines ? (int)threadIdx.x / TE : (int)threadIdx.x % TW;
-  const int te = lines ? (int)threadIdx.x % TE : (int)threadIdx.x / TW;
-  const int estep = lines ? 1 : TW;
-  const long long w = wt * TW + tw;
-  const int e = (int)(et * TE + te);
-  const bool valid = w < npos && e < K;
+  const ApplyThread d = apply_decode(bx, (int)threadIdx.x, TW, NTHREADS, K, P.inner, P.outer, lines);
+  const long long o = d.o, w = d.w;
+  const int te = d.te, estep = d.estep, e = d.e;
+  const bool valid = d.valid;
+  const long long npos = d.npos;
   const long long Ms = P.M + 2 * P.gofs;   // stored extent of the operated axis
   const long long line = lines ? (valid ? w : 0) * Ms : o * Ms * P.inner + (valid ? w : 0);
   // in lines mode the line index is the outer index and no axis follows
@@ -532,20 +524,11 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
   // not leave most threads without an element; threads then run along the
   // elements of a line and the tiles hold one column per line.
   const bool lines = LM == 2 ? (P.inner == 1 && TW > 1) : LM == 1;
-  const long long npos = lines ? P.outer : P.inner;
-  const long long wtiles = (npos + TW - 1) / TW;
-  const long long etiles = (K + TE - 1) / TE;
-  const long long et = bx % etiles;
-  bx /= etiles;
-  const long long wt = bx % wtiles;
-  const long long o = lines ? 0 : bx / wtiles;
-  const int tw = lines ? (int)threadIdx.x / TE : (int)threadIdx.x % TW;
-  const int te = lines ? (int)threadIdx.x % TE : (int)threadIdx.x / TW;
-  const int estep = lines ? 1 : TW;   // thread-index distance to the next element of the same position
-  const long long w0 = wt * TW;
-  const long long w = w0 + tw;
-  const int e = (int)(et * TE + te);
-  const bool valid = w < npos && e < K;
+  const ApplyThread d = apply_decode(bx, (int)threadIdx.x, TW, NTHREADS, K, P.inner, P.outer, lines);
+  const long long npos = d.npos, et = d.et, o = d.o, w = d.w;
+  const int tw = d.tw, te = d.te, estep = d.estep, e = d.e;
+  const bool valid = d.valid;
+  const long long w0 = d.wt * TW;
   const long long line = lines ? (valid ? w : 0) * (long long)P.M : o * (long long)P.M * P.inner + (valid ? w : 0);
   const long long plane = P.plane;
   const int rows = apply_df_rows(NORD, TE);

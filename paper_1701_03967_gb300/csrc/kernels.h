@@ -108,6 +108,39 @@ inline long long apply_tile_blocks(long long inner, long long outer, int K, int 
   return (lines ? 1 : outer) * ((npos + TW - 1) / TW) * ((K + TE - 1) / TE);
 }
 
+// Thread tid of block bx of an apply launch (the decode both apply kernels
+// use, and fem_fft_apply_block_map on the host): element tile et = bx mod
+// etiles, then position tile wt and outer index o.  Normal tiling: TW
+// consecutive positions after the axis, thread -> (tid mod TW, tid div TW);
+// lines mode (lines: inner == 1 with TW > 1): TW lines (outer indices),
+// thread -> (tid div TE, tid mod TE).  valid: the thread has an element.
+struct ApplyThread {
+  bool lines, valid;
+  int TE, tw, te, estep;
+  long long npos, et, wt, o, w;
+  int e;
+};
+__host__ __device__ inline ApplyThread apply_decode(long long bx, int tid, int TW, int nthreads, int K,
+                                                    long long inner, long long outer, bool lines) {
+  ApplyThread d;
+  d.lines = lines;
+  d.TE = nthreads / TW;
+  d.npos = lines ? outer : inner;
+  const long long wtiles = (d.npos + TW - 1) / TW;
+  const long long etiles = (K + d.TE - 1) / d.TE;
+  d.et = bx % etiles;
+  bx /= etiles;
+  d.wt = bx % wtiles;
+  d.o = lines ? 0 : bx / wtiles;
+  d.tw = lines ? tid / d.TE : tid % TW;
+  d.te = lines ? tid % d.TE : tid / TW;
+  d.estep = lines ? 1 : TW;   // thread-index distance to the next element of the same position
+  d.w = d.wt * TW + d.tw;
+  d.e = (int)(d.et * d.TE + d.te);
+  d.valid = d.w < d.npos && d.e < K;
+  return d;
+}
+
 // The double-float apply handles one or two outputs, term t writing output t;
 // an addend, a residual base or a float32 output only with one output.
 inline bool apply_df_form_ok(const ApplyParams& P) {

@@ -1,12 +1,12 @@
-// Pencil passes for long contiguous pencils (K too large for one CTA's
-// shared memory, up to 2^20 elements): the same transforms as pencil.cuh
-// (Section 3, Theorem 2; Section 4, algorithm (a)) staged through a global
-// workspace of the Q packed complex sequences of every pencil.
+// Pencil passes for long pencils (K too large for one CTA's shared memory,
+// up to 2^20 elements): the same transforms as pencil.cuh (Section 3,
+// Theorem 2; Section 4, algorithm (a)) staged through a global workspace of
+// the Q packed complex sequences of every pencil.
 //
 //   build:   element e of every pencil -> its Q complex sequence values
 //            (node sum/difference, interior even/odd combinations, sine parts
 //            times (-1)^e), stored at the Makhoul position of e (DCT-II input
-//            order) of sequence q: S[pencil][q][r].
+//            order) of sequence q.
 //   FFT:     four-step, K = K1 K2, sequences viewed as [K1][K2] row-major.
 //            Forward-order input (natural j = j1 K2 + j2): DFT over j1 (the
 //            columns), twiddle by exp(-2 pi i j2 k1 / K), DFT over j2 (the
@@ -22,6 +22,14 @@
 //            positions of k and K-k.
 //   reconstruct: the DCT-III outputs at the Makhoul positions of element e
 //            -> the n fine-grid values of e.
+//
+// Workspace layouts.  Contiguous pencils (the last axis): S[pencil][q][x],
+// a CTA of the FFT stages takes C whole rows or columns of one sequence.
+// Strided pencils (an earlier axis, pencil stride `inner`): S[q][x][pencil]
+// with the pencils of a group padded to a multiple of 16 (pencil fastest),
+// so that the build, map and reconstruct kernels read and write the field
+// and the workspace with consecutive threads on consecutive pencils, and an
+// FFT CTA takes the same row or column of C adjacent pencils.
 // Host code (run_long_pass) at the end.
 #include <cuda_runtime.h>
 
@@ -44,28 +52,86 @@ struct LongFft {
   int pitch;                    // complex values per sequence in shared memory
   int cols;                     // 1: DFTs over j1 (stride K2); 0: over j2 (contiguous)
   int twiddle;                  // multiply element (row a, column b) by exp(-2 pi i a b / K) after the DFT
-  long long nblocks_per_seq;    // CTAs per packed sequence (K / L / C)
+  long long nblocks_per_seq;    // contiguous layout: CTAs per packed sequence (K / L / C)
+  // pencil-fastest layout: CTA = (q, line, block of C pencils), lines = the
+  // rows or columns of [K1][K2] that the stage does not run along
+  int pf, lines, Q;
+  long long npad, pblocks;
 };
 
 struct LongParams {
   const void* in;
   void* out;
   int in_f64, out_f64, accum;
-  void* S;                      // workspace [pencils][Q][K] complex T
+  void* S;                      // workspace (layout above)
   long long pencils;            // pencils of this group
-  long long base;               // global index of the group's first element (pencil * M)
+  long long first;              // index of the group's first pencil (pencil = o * inner + w)
+  long long inner;              // element stride of the pencils (1: contiguous)
+  int pf;                       // pencil-fastest workspace layout (strided pencils)
+  long long npad;               // pf: pencils per workspace row (a multiple of 16)
   int K, K1, K2, M, n;
   const void* tw;               // T2 [K]  exp(-2 pi i j / K)
   const void* rot;              // T2 [K]  exp(-i pi k / (2K))
   const void* fwd;              // T [K][n][2Q]
   const void* inv;              // T [K][2Q][n]
   const void* mu;               // T [M]
-  double c;                     // divisor offset of the fused pass (1D)
+  // divisor of the fused pass: c + sum over the later axes of their a s lambda
+  // at the pencil's position w (as in the shared-memory passes)
+  double c;
+  int nother;
+  long long Mo[2];
+  const void* mu_o[2];
   int* nonfinite;
 };
 
 __device__ __forceinline__ int makhoul_inv(int e, int K) { return (e & 1) ? K - 1 - (e >> 1) : (e >> 1); }
 __device__ __forceinline__ long long tpos(int k, int K1, int K2) { return (long long)(k % K1) * K2 + k / K1; }
+
+// outer index o and inner position w of the group's pencil pen
+__device__ __forceinline__ void pencil_ow(const LongParams& P, long long pen, long long& o, long long& w) {
+  const long long gp = P.first + pen;
+  if (P.inner == 1) {
+    o = gp;
+    w = 0;
+  } else {
+    o = gp / P.inner;
+    w = gp - o * P.inner;
+  }
+}
+// field index of position m of the pencil (o, w)
+__device__ __forceinline__ long long field_at(const LongParams& P, long long o, long long w, long long m) {
+  return (o * P.M + m) * P.inner + w;
+}
+// workspace index of element x of sequence q of the group's pencil pen
+__device__ __forceinline__ long long ws_at(const LongParams& P, int Q, long long pen, int q, long long x) {
+  return P.pf ? ((long long)q * P.K + x) * P.npad + pen : (pen * Q + q) * (long long)P.K + x;
+}
+// (pencil, index) of thread-loop item t over pencils x count items: pencil
+// fastest in the pencil-fastest layout, else pencil-major
+__device__ __forceinline__ void split_item(const LongParams& P, long long t, long long count, long long& pen,
+                                           int& i) {
+  if (P.pf) {
+    const long long q = t / P.pencils;
+    i = (int)q;
+    pen = t - q * P.pencils;
+  } else {
+    pen = t / count;
+    i = (int)(t - pen * count);
+  }
+}
+// c + the later axes' eigenvalue terms at the pencil's inner position w
+template <typename T>
+__device__ __forceinline__ T divisor_base(const LongParams& P, long long w) {
+  double b = P.c;
+  if (P.nother == 1) {
+    b += double(reinterpret_cast<const T*>(P.mu_o[0])[w]);
+  } else if (P.nother == 2) {
+    const long long i1 = w / P.Mo[1], i2 = w - i1 * P.Mo[1];
+    b += double(reinterpret_cast<const T*>(P.mu_o[0])[i1]);
+    b += double(reinterpret_cast<const T*>(P.mu_o[1])[i2]);
+  }
+  return T(b);
+}
 
 template <typename T>
 __device__ __forceinline__ T load_in(const LongParams& P, long long idx, bool& nf) {
@@ -100,25 +166,26 @@ __global__ void __launch_bounds__(kLongThreads) long_build_kernel(LongParams P) 
   bool nf = false;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const long long pen = t / P.K;
-    const int e = (int)(t - pen * P.K);
-    const long long g0 = P.base + pen * P.M + (long long)NORD * e;   // first value of element e
+    long long pen, o, w;
+    int e;
+    split_item(P, t, P.K, pen, e);
+    pencil_ow(P, pen, o, w);
+    const long long m0 = (long long)NORD * e;   // first value of element e
     T y[NORD];
 #pragma unroll
     for (int s = 0; s < NORD; ++s) {
       const bool last_vertex = (s == NORD - 1) && (e == P.K - 1);   // the right boundary node: not stored
-      y[s] = last_vertex ? T(0) : load_in<T>(P, g0 + s, nf);
+      y[s] = last_vertex ? T(0) : load_in<T>(P, field_at(P, o, w, m0 + s), nf);
     }
-    const T xl = e > 0 ? load_in<T>(P, g0 - 1, nf) : T(0);
+    const T xl = e > 0 ? load_in<T>(P, field_at(P, o, w, m0 - 1), nf) : T(0);
     const T xr = y[NORD - 1];
     const T sg = (e & 1) ? T(-1) : T(1);
     const int r = makhoul_inv(e, P.K);
-    cpx<T>* dst = S + (pen * Q) * P.K + r;
-    dst[0] = cpx<T>{sg * (xr + xl), xr - xl};
+    S[ws_at(P, Q, pen, 0, r)] = cpx<T>{sg * (xr + xl), xr - xl};
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
-      if (2 * q < NORD) dst[(long long)q * P.K] = cpx<T>{sg * (y[q - 1] + y[NORD - q - 1]), y[q - 1] - y[NORD - q - 1]};
-      else dst[(long long)q * P.K] = cpx<T>{sg * y[q - 1], T(0)};
+      if (2 * q < NORD) S[ws_at(P, Q, pen, q, r)] = cpx<T>{sg * (y[q - 1] + y[NORD - q - 1]), y[q - 1] - y[NORD - q - 1]};
+      else S[ws_at(P, Q, pen, q, r)] = cpx<T>{sg * y[q - 1], T(0)};
     }
   }
   if (__syncthreads_or(nf) && threadIdx.x == 0 && P.nonfinite) atomicOr(P.nonfinite, 1);
@@ -140,17 +207,37 @@ __global__ void __launch_bounds__(kLongThreads) long_fft_kernel(LongParams P, Lo
   const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(P.tw);
   cpx<T>* S = reinterpret_cast<cpx<T>*>(P.S);
   const int K = P.K, L = F.L, C = F.C;
-  const long long seq = blockIdx.x / F.nblocks_per_seq;
-  const long long blk = blockIdx.x - seq * F.nblocks_per_seq;
-  cpx<T>* base = S + seq * K;
-  // element x of local sequence c: global offset
-  const int c0 = (int)(blk * C);
-  auto goff = [&](int c, int x) -> long long {
-    return F.cols ? (long long)x * P.K2 + (c0 + c) : (long long)(c0 + c) * P.K2 + x;
-  };
+  // element x of local sequence c sits at S[off0 + x xs + c cs]; `other` is
+  // the coordinate of [K1][K2] the stage does not run along (row or column)
+  long long off0, xs, cs;
+  int other0, other_c;   // other = other0 + other_c * c
+  if (!F.pf) {
+    const long long seq = blockIdx.x / F.nblocks_per_seq;
+    const long long blk = blockIdx.x - seq * F.nblocks_per_seq;
+    const int c0 = (int)(blk * C);
+    off0 = seq * K + (F.cols ? c0 : (long long)c0 * P.K2);
+    xs = F.cols ? P.K2 : 1;
+    cs = F.cols ? 1 : P.K2;
+    other0 = c0;
+    other_c = 1;
+  } else {
+    const long long pb = blockIdx.x % F.pblocks;
+    const long long rest = blockIdx.x / F.pblocks;
+    const int line = (int)(rest % F.lines);
+    const int q = (int)(rest / F.lines);
+    const long long x0 = F.cols ? line : (long long)line * P.K2;
+    off0 = ((long long)q * K + x0) * F.npad + pb * C;
+    xs = (F.cols ? (long long)P.K2 : 1LL) * F.npad;
+    cs = 1;
+    other0 = line;
+    other_c = 0;
+  }
+  auto goff = [&](int c, int x) -> long long { return off0 + (long long)x * xs + (long long)c * cs; };
+  cpx<T>* base = S;
+  const bool lanes_c = F.cols || F.pf;   // lanes over c where c is the contiguous index
   for (int t = threadIdx.x; t < C * L; t += blockDim.x) {
     int c, x;
-    if (F.cols) {   // lanes over the C adjacent columns: coalesced rows
+    if (lanes_c) {   // lanes over the C adjacent columns or pencils: coalesced rows
       x = t / C;
       c = t - x * C;
     } else {
@@ -197,7 +284,7 @@ __global__ void __launch_bounds__(kLongThreads) long_fft_kernel(LongParams P, Lo
   }
   for (int t = threadIdx.x; t < C * L; t += blockDim.x) {
     int c, x;
-    if (F.cols) {
+    if (lanes_c) {
       x = t / C;
       c = t - x * C;
     } else {
@@ -207,7 +294,8 @@ __global__ void __launch_bounds__(kLongThreads) long_fft_kernel(LongParams P, Lo
     cpx<T> v = A[c * F.pitch + x];
     if (F.twiddle) {
       // element at (row a, column b) of [K1][K2]: exp(-2 pi i a b / K)
-      const long long a = F.cols ? x : (c0 + c), b = F.cols ? (c0 + c) : x;
+      const long long oth = other0 + (long long)other_c * c;
+      const long long a = F.cols ? x : oth, b = F.cols ? oth : x;
       v = cmul(v, ld_cpx<T>(tw, (int)((a * b) % K)));
     }
     base[goff(c, x)] = v;
@@ -237,19 +325,19 @@ __global__ void __launch_bounds__(kLongThreads) long_map_kernel(LongParams P) {
   bool nf = false;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const long long pen = t / half;
-    const int tau = (int)(t - pen * half);
+    long long pen, o, w;
+    int tau;
+    split_item(P, t, half, pen, tau);
+    pencil_ow(P, pen, o, w);
     const int k1 = tau, k2 = tau ? K - tau : half;
-    cpx<T>* seq = S + pen * Q * K;
     const long long p1 = tpos(k1, P.K1, P.K2), p2 = tpos(k2, P.K1, P.K2);
     const cpx<T> rk = ld_cpx<T>(rot, tau ? tau : half);
-    const long long g0 = P.base + pen * P.M;   // the pencil's first value
     T w1[NORD], w2[NORD];                      // the spectral values of k1 and k2
     if (FWD) {
       T X1[Q2], X2[Q2];
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const cpx<T> v1 = seq[(long long)q * K + p1], v2 = seq[(long long)q * K + p2];
+        const cpx<T> v1 = S[ws_at(P, Q, pen, q, p1)], v2 = S[ws_at(P, Q, pen, q, p2)];
         const cpx<T> A2 = cmul(rk, v2), B2 = cmul(cpx<T>{rk.re, -rk.im}, v2);
         if (tau) {
           const cpx<T> A = cmul(rk, v1);
@@ -286,23 +374,24 @@ __global__ void __launch_bounds__(kLongThreads) long_map_kernel(LongParams P) {
 #pragma unroll
         for (int l = 0; l < NORD; ++l) {
           const int s1 = tau ? NORD * k1 - 1 + l : l - 1;   // spectral index of (k1, l)
-          if (s1 >= 0) store_out<T>(P, g0 + s1, w1[l]);
-          store_out<T>(P, g0 + NORD * k2 - 1 + l, w2[l]);
+          if (s1 >= 0) store_out<T>(P, field_at(P, o, w, s1), w1[l]);
+          store_out<T>(P, field_at(P, o, w, (long long)NORD * k2 - 1 + l), w2[l]);
         }
         continue;
       }
+      const T b0 = divisor_base<T>(P, w);
 #pragma unroll
       for (int l = 0; l < NORD; ++l) {
         const int s1 = tau ? NORD * k1 - 1 + l : l - 1;
-        w1[l] = s1 >= 0 ? w1[l] / (T(P.c) + mu[s1]) : T(0);
-        w2[l] = w2[l] / (T(P.c) + mu[NORD * k2 - 1 + l]);
+        w1[l] = s1 >= 0 ? w1[l] / (b0 + mu[s1]) : T(0);
+        w2[l] = w2[l] / (b0 + mu[NORD * k2 - 1 + l]);
       }
     } else {
 #pragma unroll
       for (int l = 0; l < NORD; ++l) {
         const int s1 = tau ? NORD * k1 - 1 + l : l - 1;
-        w1[l] = s1 >= 0 ? load_in<T>(P, g0 + s1, nf) : T(0);
-        w2[l] = load_in<T>(P, g0 + NORD * k2 - 1 + l, nf);
+        w1[l] = s1 >= 0 ? load_in<T>(P, field_at(P, o, w, s1), nf) : T(0);
+        w2[l] = load_in<T>(P, field_at(P, o, w, (long long)NORD * k2 - 1 + l), nf);
       }
     }
     if (INV) {
@@ -327,11 +416,11 @@ __global__ void __launch_bounds__(kLongThreads) long_map_kernel(LongParams P) {
       for (int q = 0; q < Q; ++q) {
         const T a1 = o1[2 * q], b1 = o1[2 * q + 1], a2 = o2[2 * q], b2 = o2[2 * q + 1];
         if (tau) {
-          seq[(long long)q * K + p1] = cmul(rk, cpx<T>{a2 - b2, a1 + b1});
-          seq[(long long)q * K + p2] = cmul(rc, cpx<T>{a1 - b1, a2 + b2});
+          S[ws_at(P, Q, pen, q, p1)] = cmul(rk, cpx<T>{a2 - b2, a1 + b1});
+          S[ws_at(P, Q, pen, q, p2)] = cmul(rc, cpx<T>{a1 - b1, a2 + b2});
         } else {
-          seq[(long long)q * K + p1] = cpx<T>{a1, b1};
-          seq[(long long)q * K + p2] = cmul(rk, cpx<T>{a2 - b2, a2 + b2});
+          S[ws_at(P, Q, pen, q, p1)] = cpx<T>{a1, b1};
+          S[ws_at(P, Q, pen, q, p2)] = cmul(rk, cpx<T>{a2 - b2, a2 + b2});
         }
       }
     }
@@ -348,17 +437,18 @@ __global__ void __launch_bounds__(kLongThreads) long_reconstruct_kernel(LongPara
   const cpx<T>* S = reinterpret_cast<const cpx<T>*>(P.S);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const long long pen = t / P.K;
-    const int e = (int)(t - pen * P.K);
+    long long pen, o, w;
+    int e;
+    split_item(P, t, P.K, pen, e);
+    pencil_ow(P, pen, o, w);
     const int r = makhoul_inv(e, P.K);
-    const cpx<T>* src = S + pen * Q * P.K + r;
     const T sg = (e & 1) ? T(-1) : T(1);
     T y[NORD];
-    const cpx<T> x0 = src[0];
+    const cpx<T> x0 = S[ws_at(P, Q, pen, 0, r)];
     y[NORD - 1] = sg * x0.re + x0.im;
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
-      const cpx<T> x = src[(long long)q * P.K];
+      const cpx<T> x = S[ws_at(P, Q, pen, q, r)];
       const T ys = sg * x.re, yc = x.im;
       if (2 * q < NORD) {
         y[q - 1] = ys + yc;
@@ -367,10 +457,10 @@ __global__ void __launch_bounds__(kLongThreads) long_reconstruct_kernel(LongPara
         y[q - 1] = ys;
       }
     }
-    const long long g0 = P.base + pen * P.M + (long long)NORD * e;
+    const long long m0 = (long long)NORD * e;
 #pragma unroll
     for (int s = 0; s < NORD; ++s)
-      if (!(s == NORD - 1 && e == P.K - 1)) store_out<T>(P, g0 + s, y[s]);
+      if (!(s == NORD - 1 && e == P.K - 1)) store_out<T>(P, field_at(P, o, w, m0 + s), y[s]);
   }
 }
 
@@ -392,7 +482,10 @@ void long_split(int K, int* K1, int* K2) {
   *K2 = K / k1;
 }
 
-bool long_stage(int L, int count, int elem_bytes, bool cols, bool twiddle, LongFft* F) {
+// One FFT stage of length L.  Contiguous layout: count = sequences of length
+// L per packed sequence, C of them per CTA (C | count).  Pencil-fastest
+// layout (pf): count = lines of the stage, C adjacent pencils per CTA.
+bool long_stage(int L, int count, int elem_bytes, bool cols, bool twiddle, bool pf, int Q, LongFft* F) {
   std::memset(F, 0, sizeof(*F));
   F->L = L;
   int r = L;
@@ -409,12 +502,20 @@ bool long_stage(int L, int count, int elem_bytes, bool cols, bool twiddle, LongF
   F->pitch = L + 1;
   const long long budget = 96 * 1024;
   int C = 1;
-  while (C * 2 <= 16 && count % (C * 2) == 0 && 2LL * (C * 2) * F->pitch * elem_bytes <= budget) C *= 2;
+  if (pf) {
+    C = 16;
+    while (C > 1 && 2LL * C * F->pitch * elem_bytes > budget) C /= 2;
+  } else {
+    while (C * 2 <= 16 && count % (C * 2) == 0 && 2LL * (C * 2) * F->pitch * elem_bytes <= budget) C *= 2;
+  }
   if (2LL * C * F->pitch * elem_bytes > 200 * 1024) return false;
   F->C = C;
   F->cols = cols ? 1 : 0;
   F->twiddle = twiddle ? 1 : 0;
-  F->nblocks_per_seq = count / C;
+  F->pf = pf ? 1 : 0;
+  F->Q = Q;
+  if (pf) F->lines = count;
+  else F->nblocks_per_seq = count / C;
   return true;
 }
 
@@ -464,30 +565,38 @@ int long_fft(const LongParams& P, const LongFft& F, long long nseq, cudaStream_t
   const size_t smem = 2 * (size_t)F.C * F.pitch * sizeof(cpx<T>);
   const int e = ensure_dyn_smem((const void*)long_fft_kernel<T>, smem);
   if (e) return e;
-  const long long grid = nseq * F.nblocks_per_seq;
+  const long long grid = F.pf ? (long long)F.Q * F.lines * F.pblocks : nseq * F.nblocks_per_seq;
   if (grid > 0x7fffffffLL) return (int)cudaErrorInvalidConfiguration;
   long_fft_kernel<T><<<(unsigned)grid, kLongThreads, smem, s>>>(P, F);
   return (int)cudaGetLastError();
 }
 
 template <typename T>
-int long_pass_t(fem_fft_plan p, int mode, int axis, long long outer, const void* in, bool in_f64, void* out,
-                bool out_f64, bool accum, int* nonfinite, cudaStream_t s) {
+int long_pass_t(fem_fft_plan p, int mode, int axis, long long outer, long long inner, const void* in, bool in_f64,
+                void* out, bool out_f64, bool accum, int* nonfinite, cudaStream_t s) {
   const AxisHost& ax = p->ax[axis];
   const int n = ax.n, K = ax.K, M = ax.M, Q = n / 2 + 1;
   const DevTables& d = sizeof(T) == 8 ? p->t64[axis] : p->t32[axis];
+  const bool pf = inner > 1;
   int K1, K2;
   long_split(K, &K1, &K2);
+  // contiguous layout: count = the other factor (C columns / rows of one
+  // sequence per CTA); pencil-fastest layout: count = lines of the stage
   LongFft cols_tw, rows, rows_tw, cols;
-  if (!long_stage(K1, K2, sizeof(cpx<T>), true, true, &cols_tw) || !long_stage(K2, K1, sizeof(cpx<T>), false, false, &rows) ||
-      !long_stage(K2, K1, sizeof(cpx<T>), false, true, &rows_tw) || !long_stage(K1, K2, sizeof(cpx<T>), true, false, &cols)) {
+  const int eb = sizeof(cpx<T>);
+  if (!long_stage(K1, K2, eb, true, true, pf, Q, &cols_tw) || !long_stage(K2, K1, eb, false, false, pf, Q, &rows) ||
+      !long_stage(K2, K1, eb, false, true, pf, Q, &rows_tw) || !long_stage(K1, K2, eb, true, false, pf, Q, &cols)) {
     set_last_error("long pencil: no FFT schedule");
     return FEM_FFT_ERR_ARG;
   }
-  // workspace: the packed sequences of a group of pencils (at most 256 MiB)
+  // workspace: the packed sequences of a group of pencils (at most 256 MiB;
+  // pencil-fastest groups are multiples of 16 pencils)
+  const long long total = outer * inner;
   const size_t per_pencil = (size_t)Q * K * sizeof(cpx<T>);
-  const long long group = std::max<long long>(1, std::min<long long>(outer, (256LL << 20) / (long long)per_pencil));
-  const size_t need = (size_t)group * per_pencil;
+  long long group = std::max<long long>(1, std::min<long long>(total, (256LL << 20) / (long long)per_pencil));
+  if (pf) group = std::max<long long>(16, group / 16 * 16);
+  const long long gpad = pf ? (group + 15) / 16 * 16 : group;
+  const size_t need = (size_t)gpad * per_pencil;
   if (p->long_ws_bytes < need) {
     if (p->long_ws) {
       cudaStreamSynchronize(s);
@@ -510,6 +619,8 @@ int long_pass_t(fem_fft_plan p, int mode, int axis, long long outer, const void*
   P.out_f64 = out_f64;
   P.accum = accum;
   P.S = p->long_ws;
+  P.inner = inner;
+  P.pf = pf ? 1 : 0;
   P.K = K;
   P.K1 = K1;
   P.K2 = K2;
@@ -521,11 +632,23 @@ int long_pass_t(fem_fft_plan p, int mode, int axis, long long outer, const void*
   P.inv = d.inv;
   P.mu = d.mu;
   P.c = p->c;
+  if (mode == MODE_FUSED) {   // the fused pass runs along axis 0: w indexes the later axes
+    P.nother = p->N - 1;
+    for (int j = 1; j < p->N; ++j) {
+      P.Mo[j - 1] = p->M[j];
+      P.mu_o[j - 1] = sizeof(T) == 8 ? p->t64[j].mu : p->t32[j].mu;
+    }
+  }
   P.nonfinite = nonfinite;
   int e = 0;
-  for (long long g0 = 0; g0 < outer && !e; g0 += group) {
-    P.pencils = std::min(group, outer - g0);
-    P.base = g0 * M;
+  for (long long g0 = 0; g0 < total && !e; g0 += group) {
+    P.pencils = std::min(group, total - g0);
+    P.first = g0;
+    P.npad = pf ? (P.pencils + 15) / 16 * 16 : 0;
+    for (LongFft* F : {&cols_tw, &rows, &rows_tw, &cols}) {
+      F->npad = P.npad;
+      F->pblocks = pf ? P.npad / F->C : 0;
+    }
     const long long nseq = P.pencils * Q;
     const unsigned gridK = (unsigned)std::min<long long>((P.pencils * K + kLongThreads - 1) / kLongThreads, 152LL * 64);
     const unsigned gridH = (unsigned)std::min<long long>((P.pencils * (K / 2) + kLongThreads - 1) / kLongThreads, 152LL * 64);
@@ -547,14 +670,14 @@ int long_pass_t(fem_fft_plan p, int mode, int axis, long long outer, const void*
 
 }  // namespace
 
-int run_long_pass(fem_fft_plan p, int mode, int axis, long long outer, const void* in, bool in_f64, void* out,
-                  bool out_f64, bool accum, bool f64, int* nonfinite, cudaStream_t s) {
-  if (mode == MODE_FUSED && p->N != 1) {
-    set_last_error("long pencils: the fused pass only in 1D");
+int run_long_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inner, const void* in,
+                  bool in_f64, void* out, bool out_f64, bool accum, bool f64, int* nonfinite, cudaStream_t s) {
+  if (mode == MODE_FUSED && axis != 0) {
+    set_last_error("long pencils: the fused pass runs along axis 0");
     return FEM_FFT_ERR_ARG;
   }
-  return f64 ? long_pass_t<double>(p, mode, axis, outer, in, in_f64, out, out_f64, accum, nonfinite, s)
-             : long_pass_t<float>(p, mode, axis, outer, in, in_f64, out, out_f64, accum, nonfinite, s);
+  return f64 ? long_pass_t<double>(p, mode, axis, outer, inner, in, in_f64, out, out_f64, accum, nonfinite, s)
+             : long_pass_t<float>(p, mode, axis, outer, inner, in, in_f64, out, out_f64, accum, nonfinite, s);
 }
 
 }  // namespace femfft

@@ -338,6 +338,16 @@ __device__ __forceinline__ long long pencil_base(const PassGeom& g, long long ti
 
 constexpr int kLoadBatch = 8;   // independent global accesses in flight per thread
 
+// j / M for the flat index j of a tile of contiguous pencils (j < 2^24): a
+// float product truncated, then corrected by one step each way (the product
+// is off by less than one for j below 2^24).
+__device__ __forceinline__ int tile_pencil(int j, int M, float invM) {
+  int p = (int)((float)j * invM);
+  if (p * M > j) --p;
+  else if ((p + 1) * M <= j) ++p;
+  return p;
+}
+
 // Field loads.  NC: through the read-only data cache (the field is not
 // written while the kernel runs); otherwise L2-coherent loads (the batched
 // kernel reads fields that other CTAs of the same launch wrote).
@@ -395,10 +405,48 @@ __device__ bool load_tile(T* smr, const PassParams& P, long long tile, bool spec
     }
   };
   if (g.inner == 1) {
-    for (int p = 0; p < g.W; ++p) {
-      const long long base = pencil_base(g, tile, p);
-      T* dst = smr + 2 * p * P.pitch;
-      for (int i0 = threadIdx.x; i0 < M; i0 += kLoadBatch * blockDim.x) batch(dst, i0, blockDim.x, base, 1);
+    // the tile's pencils are one contiguous range of np * M values: swept
+    // flat (short pencils would leave most of a per-pencil batch idle)
+    const long long first = tile * g.W;
+    const int np = (int)min((long long)g.W, g.outer - first);
+    const int L = np * M;
+    const long long base = first * M;
+    const float invM = 1.0f / (float)M;
+    for (int j0 = threadIdx.x; j0 < L; j0 += kLoadBatch * blockDim.x) {
+      if (P.in_f64) {
+        double x[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int j = j0 + u * blockDim.x;
+          x[u] = j < L ? ld_field<NC>(ind + base + j) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int j = j0 + u * blockDim.x;
+          if (check) nf |= nonfinite_f64(x[u]);
+          T v;
+          from_f64(x[u], v);
+          if (j < L) {
+            const int pp = tile_pencil(j, M, invM);
+            smr[2 * pp * P.pitch + chunk_slot<NORD, Q2>(j - pp * M + sh)] = v;
+          }
+        }
+      } else {
+        float x[kLoadBatch];
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int j = j0 + u * blockDim.x;
+          x[u] = j < L ? ld_field<NC>(inf + base + j) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kLoadBatch; ++u) {
+          const int j = j0 + u * blockDim.x;
+          if (j < L) {
+            const int pp = tile_pencil(j, M, invM);
+            smr[2 * pp * P.pitch + chunk_slot<NORD, Q2>(j - pp * M + sh)] = T(x[u]);
+          }
+        }
+      }
     }
     return nf;
   }
@@ -428,13 +476,15 @@ __device__ void store_tile(const T* smr, const PassParams& P, long long tile, bo
   const PassGeom& g = P.g;
   const int M = g.M;
   const int sh = spectral ? 1 : 0;
-  if (g.inner == 1) {
-    for (int p = 0; p < g.W; ++p) {
-      const long long base = pencil_base(g, tile, p);
-      if (base < 0) continue;
-      const T* src = smr + 2 * p * P.pitch;
-      for (int i = threadIdx.x; i < M; i += blockDim.x)
-        store_one<T, NC>(P, base + i, src[chunk_slot<NORD, Q2>(i + sh)]);
+  if (g.inner == 1) {   // flat over the tile's contiguous range, as in load_tile
+    const long long first = tile * g.W;
+    const int np = (int)min((long long)g.W, g.outer - first);
+    const int L = np * M;
+    const long long base = first * M;
+    const float invM = 1.0f / (float)M;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+      const int pp = tile_pencil(j, M, invM);
+      store_one<T, NC>(P, base + j, smr[2 * pp * P.pitch + chunk_slot<NORD, Q2>(j - pp * M + sh)]);
     }
     return;
   }

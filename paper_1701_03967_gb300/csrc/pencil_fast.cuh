@@ -41,19 +41,30 @@
 
 namespace femfft {
 
-// threads per CTA: 512 for the V = 16 schedules; 320 (ten warps, 204
-// registers per thread) for V = 32, whose FFT holds 32 complex values per
-// thread (at 128 registers ptxas spills)
-template <int V>
+// Launch shape of the register-radix kernels per (V, mode), compiled into
+// their launch bounds and used by the host plan:
+//   threads per CTA: 512 for the V = 16 schedules; 320 (ten warps) for
+//     V = 32, whose FFT holds 32 complex values per thread;
+//   resident CTAs per SM: two for the forward and inverse passes of the
+//     V = 32 schedules (96 registers per thread; ptxas spills about 1.3 KB
+//     per thread, but the load/store phase of one CTA overlaps the FFT and
+//     map phases of the other: measured 1.04 -> 0.69 ms (forward) and
+//     0.99 -> 0.78 ms (inverse) per 2D n = 9 K = 1024 launch against one CTA
+//     of 168 registers); one for the fused pass (strided pencils, 0.85 ->
+//     1.13 ms at two) and for V = 16.
+template <int V, int MODE>
 __host__ __device__ constexpr int fast_threads() { return V == 32 ? 320 : 512; }
-// resident CTAs per SM the kernels are compiled for: two for the forward and
-// inverse passes of the V = 32 schedules (96 registers per thread, a few
-// hundred bytes of spills, but the load/store phase of one CTA overlaps the
-// FFT and map phases of the other: measured 1.04 -> 0.69 ms (forward) and
-// 0.99 -> 0.78 ms (inverse) per 2D n = 9 K = 1024 launch); one for the fused
-// pass (strided pencils, 0.85 -> 1.13 ms at two) and for V = 16
 template <int V, int MODE>
 __host__ __device__ constexpr int fast_min_blocks() { return (V == 32 && MODE != 2) ? 2 : 1; }
+// the same at run time (host)
+inline int fast_threads_rt(int V, int mode) {
+  if (V == 32) return mode == 2 ? fast_threads<32, 2>() : fast_threads<32, 0>();
+  return fast_threads<16, 0>();
+}
+inline int fast_ctas_rt(int V, int mode) {
+  if (V == 32) return mode == 2 ? fast_min_blocks<32, 2>() : fast_min_blocks<32, 0>();
+  return fast_min_blocks<16, 0>();
+}
 // chunks per thread of the sequence build (W K <= kFastChunkTasks threads)
 constexpr int kFastChunkTasks = 16;
 
@@ -824,7 +835,7 @@ __device__ __forceinline__ void fast_tile(const FastParams& P, long long tile, u
 // so that those loads do not wait on HBM latency.  (A persistent loop over
 // tiles would do the same but made ptxas spill heavily.)
 template <typename T, int NORD, int MODE, int V>
-__global__ void __launch_bounds__(fast_threads<V>(), (fast_min_blocks<V, MODE>())) pencil_fast_kernel(FastParams P) {
+__global__ void __launch_bounds__(fast_threads<V, MODE>(), (fast_min_blocks<V, MODE>())) pencil_fast_kernel(FastParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T den_base[kMaxW];
   const long long tile = blockIdx.x;

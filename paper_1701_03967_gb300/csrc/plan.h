@@ -68,14 +68,16 @@ void set_fft_passes(PassParams& P);
 constexpr int kPitchSlack = 16;
 int tile_pitch(int K, int Q, int V, int W, bool strided, int elem_bytes);
 
+// A pencil pass over pencils too long for one CTA's shared memory
+// (longpass.cu): global-memory four-step FFT path.  outer x inner pencils
+// (inner: their element stride, 1 for the contiguous axis); f64: the pass's
+// arithmetic.
+int run_long_pass(fem_fft_plan p, int mode, int axis, long long outer, long long inner, const void* in,
+                  bool in_f64, void* out, bool out_f64, bool accum, bool f64, int* nonfinite, cudaStream_t s);
+
 // Records the mixed-precision solve of nrhs right-hand sides (b -> u, then
 // `steps` refinement steps) as the plan would launch it.  nrhs must not
 // exceed the plan's max_nrhs.  b and u may be placeholder addresses.
-// A pencil pass over contiguous pencils too long for one CTA's shared memory
-// (longpass.cu): global-memory four-step FFT path.  f64: the pass's arithmetic.
-int run_long_pass(fem_fft_plan p, int mode, int axis, long long outer, const void* in, bool in_f64, void* out,
-                  bool out_f64, bool accum, bool f64, int* nonfinite, cudaStream_t s);
-
 int record_mixed_solve(fem_fft_plan p, const double* b, double* u, long long nrhs, int steps,
                        std::vector<RecordedOp>* ops);
 

@@ -1,17 +1,13 @@
 """Host logic of the apply launches (no GPU): the block tiling returned by
-fem_fft_apply_tiling, run through the thread -> (position, element) mapping
-the apply kernels use, must give every (position, element) pair of the axis
-to exactly one thread, and every thread's element slots must fit the block
-(256 threads, TW positions x 256 / TW elements).
-
-Mapping of a block bx (the kernels' decode): element tile et = bx mod
-etiles, then position tile and outer index.  Normal tiling: positions are
-the `inner` positions after the axis, thread t -> (t mod TW, t div TW).
-Lines mode (inner == 1, TW > 1): positions are the `outer` lines, thread t
--> (t div TE, t mod TE), one element tile row per line."""
+fem_fft_apply_tiling and the thread map of every block returned by
+fem_fft_apply_block_map -- computed by the decode the apply kernels
+themselves run -- must give every (outer index, position, element) triple
+of the axis to exactly one thread of one block, with the thread's element
+slot inside the block (256 threads, TW positions x 256 / TW elements)."""
 
 import ctypes
 
+import numpy as np
 import pytest
 
 NT = 256
@@ -26,27 +22,34 @@ def _tiling(inner, outer, K):
     return tw.value, blocks.value
 
 
+def _block_map(inner, outer, K, bx):
+    from paper_1701_03967_gb300 import _lib
+    o = np.empty(NT, np.int64)
+    w = np.empty(NT, np.int64)
+    e = np.empty(NT, np.int64)
+    p = ctypes.POINTER(ctypes.c_int64)
+    rc = _lib.lib().fem_fft_apply_block_map(inner, outer, K, bx, o.ctypes.data_as(p), w.ctypes.data_as(p),
+                                            e.ctypes.data_as(p))
+    assert rc == 0
+    return o, w, e
+
+
 def _cover(inner, outer, K):
     TW, B = _tiling(inner, outer, K)
     assert 1 <= TW <= 32 and NT % TW == 0
-    TE = NT // TW
     lines = inner == 1 and TW > 1
     npos = outer if lines else inner
-    etiles = (K + TE - 1) // TE
-    wtiles = (npos + TW - 1) // TW
-    assert B == (1 if lines else outer) * wtiles * etiles
-    seen = {}
-    for bx0 in range(B):
-        et, bx = bx0 % etiles, bx0 // etiles
-        wt, o = bx % wtiles, (0 if lines else bx // wtiles)
-        for t in range(NT):
-            tw, te = (t // TE, t % TE) if lines else (t % TW, t // TW)
-            w, e = wt * TW + tw, et * TE + te
-            if w < npos and e < K:
-                key = (o, w, e)
-                seen[key] = seen.get(key, 0) + 1
-    want = (1 if lines else outer) * npos * K
-    assert len(seen) == want and all(v == 1 for v in seen.values())
+    nouter = 1 if lines else outer
+    seen = np.zeros((nouter, npos, K), np.int32)
+    for bx in range(B):
+        o, w, e = _block_map(inner, outer, K, bx)
+        has = e >= 0
+        assert np.all((o[has] >= 0) & (o[has] < nouter))
+        assert np.all((w[has] >= 0) & (w[has] < npos))
+        assert np.all((e[has] >= 0) & (e[has] < K))
+        assert np.all((o[~has] == -1) & (w[~has] == -1))
+        np.add.at(seen, (o[has], w[has], e[has]), 1)
+    assert np.all(seen == 1)
     return TW, lines
 
 
@@ -68,7 +71,13 @@ def test_lines_mode_keeps_threads_busy():
         assert K / (NT // TW) >= 0.5
 
 
-def test_rejects_non_positive_sizes():
+def test_rejects_non_positive_sizes_and_blocks_outside_the_launch():
     from paper_1701_03967_gb300 import _lib
     for args in [(0, 1, 8), (1, 0, 8), (1, 1, 0), (-1, 1, 8)]:
         assert _lib.lib().fem_fft_apply_tiling(*args, None, None) != 0
+    _, B = _tiling(3, 5, 6)
+    o = np.empty(NT, np.int64)
+    p = o.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    for bx in (-1, B):
+        assert _lib.lib().fem_fft_apply_block_map(3, 5, 6, bx, p, p, p) != 0
+    assert _lib.lib().fem_fft_apply_block_map(3, 5, 6, 0, None, p, p) != 0

@@ -88,3 +88,64 @@ def test_long_mixed_solve_matches_fp64():
     assert rel <= 1e-10, rel
     p64.close()
     pmx.close()
+
+
+# Strided long pencils: an earlier axis of a 2D/3D field too long for one
+# CTA (pencil-fastest workspace, group padded to 16 pencils).  Axis 0 long:
+# the fused forward/divide/inverse pass on the long path, its divisor taking
+# the later axes' eigenvalues (one or two of them); a middle axis long: the
+# forward and inverse passes with pencils strided by the last axis.
+STRIDED_CASES = [
+    dict(n=(1, 2), K=(8192, 4), a=(1.0, 2.0), c=0.5),       # fused pass long, 7 pencils per outer index
+    dict(n=(1, 1, 2), K=(6144, 2, 2), a=(1.0, 1.5, 0.7), c=0.0),   # fused long, two later axes, K = 3 * 2^11
+    dict(n=(2, 1, 2), K=(2, 6144, 2), a=(0.8, 1.0, 1.3), c=1.0),   # middle axis long
+]
+
+
+def _bubble_signs(plan, prob):
+    """Signs of the oracle's bubble vectors relative to the plan's, as one
+    array over the field (the free signs of Theorem 1's element modes)."""
+    sgs = []
+    for i in range(prob.N):
+        n = prob.ns[i]
+        sg = np.ones(prob.M[i])
+        if n >= 2:
+            _, _, p = plan.axis_tables(i)
+            _, S, _ = prob.basis1d(i)
+            for l in range(n - 1):
+                sg[l] = np.sign(p[0, l] @ S[0:n - 1, l])
+        sgs.append(sg)
+    out = sgs[0]
+    for sg in sgs[1:]:
+        out = np.multiply.outer(out, sg)
+    return out
+
+
+@pytest.mark.parametrize("case", STRIDED_CASES, ids=lambda c: "n" + "x".join(map(str, c["n"])) + "_K" +
+                         "x".join(map(str, c["K"])))
+def test_strided_long_pencils_match_oracle(case):
+    from paper_1701_03967_gb300 import Plan
+    prob = osolve.Problem(case["n"], case["K"], None, case["a"], case["c"])
+    p64 = Plan(case["n"], case["K"], None, case["a"], case["c"], "fp64", max_nrhs=2)
+    y = synth.normal_batch(2, prob.M, synth.CFG_TEST, 610)
+    yt = torch.from_numpy(y).cuda()
+    sg = _bubble_signs(p64, prob)
+    got = p64.forward(yt).cpu().numpy()
+    want = osolve.forward_coefficients(prob, y)
+    assert _rel(got * sg, want) <= 1e-12
+    assert _relmax(got * sg, want) <= 1e-12
+    w = synth.normal_batch(2, prob.M, synth.CFG_TEST, 611)
+    gw = p64.inverse(torch.from_numpy(w * sg).cuda()).cpu().numpy()
+    want_w = osolve.inverse_expansion(prob, w)
+    assert _rel(gw, want_w) <= 1e-12
+    assert _relmax(gw, want_w) <= 1e-12
+    want_u = osolve.solve(prob, y)
+    u = p64.solve(yt).cpu().numpy()
+    assert _rel(u, want_u) <= 1e-12
+    assert _relmax(u, want_u) <= 1e-12
+    pmx = Plan(case["n"], case["K"], None, case["a"], case["c"], "mixed", max_nrhs=2)
+    um = pmx.solve(yt).cpu().numpy()
+    assert _rel(um, want_u) <= 1e-10
+    assert _relmax(um, want_u) <= 1e-10
+    p64.close()
+    pmx.close()

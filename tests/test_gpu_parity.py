@@ -326,10 +326,9 @@ def test_long_pencil_transforms_and_the_shared_memory_limit():
     """The largest float64 pencil of n = 5 that one CTA holds (K = 2048): the
     direct transform expands calC^-1 y (Theorem 2), so inverse(forward(calC
     y)) = y to float64 rounding, for a batch of pencils with a ragged count.
-    One size further (K = 3072) a contiguous pencil takes the global
-    four-step path with the same result; a strided pencil of that length
-    (axis 0 of a 2D field) is refused with an error instead of launching."""
-    from paper_1701_03967_gb300 import FemFftError
+    One size further (K = 3072) the pencil takes the global four-step path
+    with the same result, contiguous (1D) or strided (axis 0 of a 2D
+    field)."""
     g = torch.Generator(device="cuda").manual_seed(5)
     for K in (2048, 3072):
         pl = _plan(dict(n=5, K=(K,)), "fp64", max_nrhs=37)
@@ -337,7 +336,8 @@ def test_long_pencil_transforms_and_the_shared_memory_limit():
         w = pl.inverse(pl.forward(pl.apply_mass(y)))
         assert float(torch.linalg.vector_norm(w - y) / torch.linalg.vector_norm(y)) <= 1e-12, K
         pl.close()
-    big = _plan(dict(n=5, K=(3072, 2)), "fp64")
-    with pytest.raises(FemFftError):
-        big.forward(torch.zeros(big.M, dtype=torch.float64, device="cuda"))
+    big = _plan(dict(n=5, K=(3072, 2)), "fp64", max_nrhs=3)
+    y = torch.randn((3,) + tuple(big.M), dtype=torch.float64, device="cuda", generator=g)
+    w = big.inverse(big.forward(big.apply_mass(y)))
+    assert float(torch.linalg.vector_norm(w - y) / torch.linalg.vector_norm(y)) <= 1e-12
     big.close()
