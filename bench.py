@@ -250,6 +250,14 @@ def run_batched(torch, args, barrier):
     u = torch.empty_like(b)
     ms_b = time_steps(torch, lambda: batch.solve(b, out=u), max(2, args.steps // 2), args.warmup, barrier)
     batch.check()
+    # the same batch in stream mode: every problem by its own plan on one of k streams
+    us = torch.empty_like(b)
+    streams = {}
+    for k in (4, 8, 16):
+        batch.set_mode("streams", k)
+        streams[k] = time_steps(torch, lambda: batch.solve(b, out=us), max(2, args.steps // 2), args.warmup,
+                                barrier)
+    batch.set_mode("graph")
     p64 = [Plan(s["n"], s["K"], s["X"], s["a"], s["c"], "fp64", max_nrhs=s["nrhs"]) for s in specs]
     u64 = torch.empty_like(b)
     views = list(zip(p64, batch.views(b), batch.views(u64)))
@@ -273,7 +281,10 @@ def run_batched(torch, args, barrier):
            "value": units / (ms_b * 1e-3), "unit": "DOF/s", "ms_per_solve": ms_b,
            "fp64_sequential": {"value": units / (ms_64 * 1e-3), "ms_per_solve": ms_64},
            "mixed_sequential": {"value": units / (ms_mx * 1e-3), "ms_per_solve": ms_mx},
-           "rel_vs_fp64": rel, "create_s": t_create, "launches_per_solve": len({s["n"] for s in specs})}
+           "rel_vs_fp64": rel, "create_s": t_create, "launches_per_solve": len({s["n"] for s in specs}),
+           "stream_mode": {"ms_per_solve": {str(k): v for k, v in streams.items()},
+                           "value": units / (min(streams.values()) * 1e-3),
+                           "rel_vs_fp64": float(torch.linalg.vector_norm(us - u64) / torch.linalg.vector_norm(u64))}}
     batch.close()
     # the same problems with every plan on algorithm (b), batched and sequential FP64
     for pl in plans + p64:
@@ -282,9 +293,14 @@ def run_batched(torch, args, barrier):
     ms_bb = time_steps(torch, lambda: batch.solve(b, out=u), max(2, args.steps // 2), args.warmup, barrier)
     batch.check()
     rel_b = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
+    kbest = min(streams, key=streams.get)
+    batch.set_mode("streams", kbest)
+    ms_bs = time_steps(torch, lambda: batch.solve(b, out=us), max(2, args.steps // 2), args.warmup, barrier)
+    batch.set_mode("graph")
     ms_64b = time_steps(torch, seq64, max(2, args.steps // 2), args.warmup, barrier)
     out["algo_b"] = {"value": units / (ms_bb * 1e-3), "ms_per_solve": ms_bb, "steps": batch.n_steps,
                      "items": batch.n_items, "rel_vs_fp64_a": rel_b,
+                     "stream_mode": {"streams": kbest, "ms_per_solve": ms_bs, "value": units / (ms_bs * 1e-3)},
                      "fp64_sequential": {"value": units / (ms_64b * 1e-3), "ms_per_solve": ms_64b}}
     batch.close()
     for pl in p64 + plans:

@@ -418,6 +418,26 @@ int fem_fft_batch_layout(fem_fft_batch batch, int64_t* h_offsets, int64_t* total
 int fem_fft_batch_solve(fem_fft_batch batch, const double* d_b, double* d_u, void* stream);
 
 /*
+ * fem_fft_batch_set_mode -- how fem_fft_batch_solve executes (no paper
+ * counterpart; the arithmetic is the same Section 4 solve either way, the
+ * results agree to rounding).
+ *   FEM_FFT_BATCH_GRAPH    the recorded work list in one graph launch (above;
+ *                          the default)
+ *   FEM_FFT_BATCH_STREAMS  every problem solved by its own plan
+ *                          (fem_fft_solve with the batch's refinement steps,
+ *                          the plan's own tuned kernels) on one of nstreams
+ *                          (1..64) streams owned by the batch, forked from and
+ *                          joined back into the solve's stream; problems are
+ *                          assigned largest first to the least loaded stream.
+ *                          fem_fft_batch_status reports no device wait in this
+ *                          mode; each plan's fem_fft_last_info holds its status.
+ * Synchronises the device.  FEM_FFT_ERR_ARG for an unknown mode or nstreams
+ * out of range.
+ */
+enum { FEM_FFT_BATCH_GRAPH = 0, FEM_FFT_BATCH_STREAMS = 1 };
+int fem_fft_batch_set_mode(fem_fft_batch batch, int mode, int nstreams);
+
+/*
  * fem_fft_batch_status -- synchronise stream and return the status of the
  * last solve: FEM_FFT_OK, or FEM_FFT_ERR_TIMEOUT when a dependency wait gave
  * up (the results are then incomplete; *h_step names the waiting step).
@@ -475,6 +495,19 @@ int fem_fft_apply_tiling(int64_t inner, int64_t outer, int64_t K, int* h_tw, int
  */
 int fem_fft_apply_block_map(int64_t inner, int64_t outer, int64_t K, int64_t block, int64_t* h_o, int64_t* h_w,
                             int64_t* h_e);
+
+/*
+ * fem_fft_divide_check -- the float64 division of the spectral divide
+ * (Section 4, algorithm (a): coefficient / (sum_i a_i s_i lambda_i + c)) as
+ * the float64 passes compute it -- a float reciprocal seed refined by two
+ * Newton steps, then one product -- next to CUDA's float64 division, for n
+ * pairs (no paper counterpart; a diagnostic for tests).  d_q[i] = the passes'
+ * x[i] / d[i], d_ref[i] = CUDA's.  Device arrays of n float64; d[i] must lie
+ * in the float range (|d| between 2^-126 and 2^127), as every divisor of a
+ * plan does.  Asynchronous on stream.  FEM_FFT_ERR_ARG for n < 0 or a NULL
+ * pointer with n > 0.
+ */
+int fem_fft_divide_check(const double* d_x, const double* d_d, double* d_q, double* d_ref, int64_t n, void* stream);
 
 /* Static text for a status code; fem_fft_last_error: the last CUDA error
  * text recorded by this thread (empty if none). */

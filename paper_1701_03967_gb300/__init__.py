@@ -14,7 +14,7 @@ library.
 import ctypes
 
 from . import _lib
-from ._lib import FEM_FFT_FP64, FEM_FFT_MIXED, FemFftError  # noqa: F401
+from ._lib import FEM_FFT_BATCH_GRAPH, FEM_FFT_BATCH_STREAMS, FEM_FFT_FP64, FEM_FFT_MIXED, FemFftError  # noqa: F401
 
 __all__ = ["Plan", "Batch", "HeatStepper", "HostSolveStream", "FemFftError", "solve", "lib_path", "fem_solve"]
 
@@ -321,6 +321,13 @@ class Batch:
         self.total_len = total.value
         self.n_steps = nsteps.value
         self.n_items = nitems.value
+
+    def set_mode(self, mode, nstreams=8):
+        """"graph": the recorded work list in one graph launch (default);
+        "streams": every problem solved by its own plan on one of nstreams
+        streams (fem_fft_batch_set_mode)."""
+        m = {"graph": FEM_FFT_BATCH_GRAPH, "streams": FEM_FFT_BATCH_STREAMS}[mode]
+        _lib.check(_lib.lib().fem_fft_batch_set_mode(self._h, m, int(nstreams)), "fem_fft_batch_set_mode")
 
     def solve(self, b, out=None, stream=None, check=False):
         """u = L_p^{-1} b_p for every problem (packed float64 CUDA tensors)."""

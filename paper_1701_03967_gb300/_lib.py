@@ -12,6 +12,8 @@ LIB_PATH = os.path.join(_HERE, "libfemfft.so")
 
 FEM_FFT_FP64 = 0
 FEM_FFT_MIXED = 1
+FEM_FFT_BATCH_GRAPH = 0
+FEM_FFT_BATCH_STREAMS = 1
 
 _lib = None
 
@@ -74,9 +76,11 @@ def lib():
         "fem_fft_batch_tuning": ([vp, i32, PI, PD], i32),
         "fem_fft_batch_set_wait_limit": ([vp, f64], i32),
         "fem_fft_batch_hold_step": ([vp, i64], i32),
+        "fem_fft_batch_set_mode": ([vp, i32, i32], i32),
         "fem_fft_batch_order": ([i32, PI, PD, PI, PI], i32),
         "fem_fft_apply_tiling": ([i64, i64, i64, PI, ctypes.POINTER(ctypes.c_int64)], i32),
         "fem_fft_apply_block_map": ([i64, i64, i64, i64, P64, P64, P64], i32),
+        "fem_fft_divide_check": ([vp, vp, vp, vp, i64, vp], i32),
         "fem_fft_strerror": ([i32], ctypes.c_char_p),
         "fem_fft_last_error": ([], ctypes.c_char_p),
     }

@@ -1724,3 +1724,29 @@ int fem_fft_grad_coeffs(fem_fft_plan p, const double* u, const double* lam, int6
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ diagnostics
+
+namespace femfft {
+namespace {
+
+__global__ void divide_check_kernel(const double* __restrict__ x, const double* __restrict__ d, double* __restrict__ q,
+                                    double* __restrict__ ref, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    q[i] = divide_by(x[i], d[i]);
+    ref[i] = x[i] / d[i];
+  }
+}
+
+}  // namespace
+}  // namespace femfft
+
+extern "C" int fem_fft_divide_check(const double* d_x, const double* d_d, double* d_q, double* d_ref, int64_t n,
+                                    void* stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_d || !d_q || !d_ref))) return FEM_FFT_ERR_ARG;
+  if (n == 0) return FEM_FFT_OK;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 16);
+  femfft::divide_check_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d_x, d_d, d_q, d_ref, n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FEM_FFT_OK : cuda_fail(e, "divide check");
+}

@@ -425,6 +425,16 @@ struct fem_fft_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<std::pair<TuneKey, TuneVal>> tune_used;
+  // stream mode (fem_fft_batch_set_mode): every problem solved by its own
+  // plan (fem_fft_solve, the plan's fastest kernels) on one of nstreams
+  // streams, problems assigned largest first to the least loaded stream
+  std::vector<fem_fft_plan> plans;
+  std::vector<double> work;
+  int mode = FEM_FFT_BATCH_GRAPH;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  std::vector<int> order, stream_of;
 };
 
 namespace {
@@ -436,9 +446,19 @@ void drop_graph(fem_fft_batch b) {
   b->graph = nullptr;
 }
 
+void drop_streams(fem_fft_batch b) {
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  b->streams.clear();
+  b->join.clear();
+  b->fork = nullptr;
+}
+
 void free_batch(fem_fft_batch b) {
   if (!b) return;
   drop_graph(b);
+  drop_streams(b);
   for (auto& g : b->groups) {
     cudaFree(g.d_stages);
     cudaFree(g.d_item_stage);
@@ -536,6 +556,7 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
     if (pl && !uniform) {
       // the batched kernel runs every step of a problem in the launch of its
       // element order; a plan with several orders would span launches
+      free_batch(b);
       return batch_fail(FEM_FFT_ERR_ARG, "batch: plans must have one element order on every axis");
     }
     if (!pl || pl->precision != FEM_FFT_MIXED || h_nrhs[p] < 1 || h_nrhs[p] > pl->max_nrhs) {
@@ -560,6 +581,8 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
     work[p] = (double)h_nrhs[p] * (double)pl->dof;
   }
   b->total_len = off;
+  b->plans.assign(plans, plans + nprob);
+  b->work = work;
   // 2. tile shapes and radix schedules
   std::map<TuneKey, PassParams> keys;
   for (auto& ch : chains)
@@ -816,10 +839,77 @@ int fem_fft_batch_hold_step(fem_fft_batch b, int64_t step) {
   return FEM_FFT_ERR_ARG;
 }
 
+int fem_fft_batch_set_mode(fem_fft_batch b, int mode, int nstreams) {
+  if (!b || (mode != FEM_FFT_BATCH_GRAPH && mode != FEM_FFT_BATCH_STREAMS)) return FEM_FFT_ERR_ARG;
+  if (mode == FEM_FFT_BATCH_STREAMS && (nstreams < 1 || nstreams > 64)) return FEM_FFT_ERR_ARG;
+  cudaDeviceSynchronize();   // no solve of either mode may still use the streams
+  drop_streams(b);
+  b->mode = mode;
+  if (mode == FEM_FFT_BATCH_GRAPH) return FEM_FFT_OK;
+  b->streams.assign(nstreams, nullptr);
+  b->join.assign(nstreams, nullptr);
+  for (int i = 0; i < nstreams; ++i)
+    if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      drop_streams(b);
+      b->mode = FEM_FFT_BATCH_GRAPH;
+      return batch_fail(FEM_FFT_ERR_CUDA, "batch: stream mode set-up");
+    }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    drop_streams(b);
+    b->mode = FEM_FFT_BATCH_GRAPH;
+    return batch_fail(FEM_FFT_ERR_CUDA, "batch: stream mode set-up");
+  }
+  // largest problems first, each to the stream with the least work so far
+  b->order.resize(b->nprob);
+  for (int p = 0; p < b->nprob; ++p) b->order[p] = p;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return b->work[x] > b->work[y]; });
+  std::vector<double> load(nstreams, 0.0);
+  b->stream_of.assign(b->nprob, 0);
+  for (int p : b->order) {
+    const int i = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->stream_of[p] = i;
+    load[i] += b->work[p];
+  }
+  return FEM_FFT_OK;
+}
+
+namespace {
+
+// Stream mode: fork the batch streams from s, solve every problem with its
+// plan (refinement steps: the batch's), join back into s.
+int solve_streams(fem_fft_batch b, const double* d_b, double* d_u, cudaStream_t s) {
+  if (cudaEventRecord(b->fork, s) != cudaSuccess) return cuda_fail(cudaGetLastError(), "batch: fork");
+  for (cudaStream_t st : b->streams)
+    if (cudaStreamWaitEvent(st, b->fork, 0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "batch: fork");
+  int rc = FEM_FFT_OK;
+  for (int p : b->order) {
+    fem_fft_plan pl = b->plans[p];
+    const double rtol = pl->rtol;
+    const int iters = pl->max_iter;
+    pl->rtol = 0.0;
+    pl->max_iter = b->steps;
+    rc = fem_fft_solve(pl, d_b + b->offset[p], d_u + b->offset[p], b->nrhs[p], b->streams[b->stream_of[p]]);
+    pl->rtol = rtol;
+    pl->max_iter = iters;
+    if (rc) break;
+  }
+  for (size_t i = 0; i < b->streams.size(); ++i) {
+    if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess || cudaStreamWaitEvent(s, b->join[i], 0) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "batch: join");
+  }
+  return rc;
+}
+
+}  // namespace
+
 int fem_fft_batch_solve(fem_fft_batch b, const double* d_b, double* d_u, void* stream) {
   if (!b || !d_b || !d_u) return FEM_FFT_ERR_ARG;
   if ((const void*)d_b == (const void*)d_u) return batch_fail(FEM_FFT_ERR_ARG, "batch: b and u must differ");
   cudaStream_t s = (cudaStream_t)stream;
+  if (b->mode == FEM_FFT_BATCH_STREAMS) return solve_streams(b, d_b, d_u, s);
   if (!b->uploaded || d_b != b->cur_b || d_u != b->cur_u) {
     // the previous solve may still read the step tables
     if (cudaStreamSynchronize(s) != cudaSuccess) {

@@ -43,19 +43,19 @@ namespace femfft {
 
 // Launch shape of the register-radix kernels per (V, mode), compiled into
 // their launch bounds and used by the host plan:
-//   threads per CTA: 512 for the V = 16 schedules; 320 (ten warps) for
-//     V = 32, whose FFT holds 32 complex values per thread;
-//   resident CTAs per SM: two for the forward and inverse passes of the
-//     V = 32 schedules (96 registers per thread; ptxas spills about 1.3 KB
-//     per thread, but the load/store phase of one CTA overlaps the FFT and
-//     map phases of the other: measured 1.04 -> 0.69 ms (forward) and
-//     0.99 -> 0.78 ms (inverse) per 2D n = 9 K = 1024 launch against one CTA
-//     of 168 registers); one for the fused pass (strided pencils, 0.85 ->
-//     1.13 ms at two) and for V = 16.
+//   V = 32 forward and inverse passes: 160 threads (five warps), three CTAs
+//     per SM, 128 registers per thread (ptxas spills 448 B per thread; at
+//     two CTAs of 320 threads, 96 registers, it spilled 1.3 KB and the
+//     spill traffic doubled the DRAM bytes of a launch).  Measured per 2D
+//     n = 9 K = 1024 launch: forward 0.63 -> 0.57 ms, inverse 0.79 -> 0.70 ms
+//     against that shape (and 1.04 / 0.99 ms with one CTA of 168 registers);
+//   V = 32 fused pass (strided pencils): 320 threads, one CTA per SM (168
+//     registers): 0.85 ms against 0.91 ms for two CTAs of 160 threads;
+//   V = 16: 512 threads, one CTA per SM.
 template <int V, int MODE>
-__host__ __device__ constexpr int fast_threads() { return V == 32 ? 320 : 512; }
+__host__ __device__ constexpr int fast_threads() { return V == 32 ? (MODE == 2 ? 320 : 160) : 512; }
 template <int V, int MODE>
-__host__ __device__ constexpr int fast_min_blocks() { return (V == 32 && MODE != 2) ? 2 : 1; }
+__host__ __device__ constexpr int fast_min_blocks() { return (V == 32 && MODE != 2) ? 3 : 1; }
 // the same at run time (host)
 inline int fast_threads_rt(int V, int mode) {
   if (V == 32) return mode == 2 ? fast_threads<32, 2>() : fast_threads<32, 0>();

@@ -73,6 +73,26 @@ def test_small_batch_matches_oracle(small_batch):
         assert rel <= 1e-10, (c, rel)
 
 
+@pytest.mark.parametrize("nstreams", [1, 3])
+def test_stream_mode_matches_oracle_and_graph_mode(small_batch, nstreams):
+    """Stream mode (every problem by its own plan on nstreams streams) gives
+    the same solutions as the graph launch, to the mixed bar against the
+    oracle."""
+    batch, rhs, b = small_batch
+    ug = batch.solve(b, check=True).clone()
+    try:
+        batch.set_mode("streams", nstreams)
+        us = batch.solve(b)
+        torch.cuda.synchronize()
+    finally:
+        batch.set_mode("graph")
+    for c, bp, up, gp in zip(SMALL, rhs, batch.views(us), batch.views(ug)):
+        prob = osolve.Problem(c["n"], c["K"], c.get("X"), c.get("a"), c.get("c", 0.0))
+        want = osolve.solve(prob, bp)
+        assert _rel(up.cpu().numpy(), want) <= 1e-10, c
+        assert _rel(up.cpu().numpy(), gp.cpu().numpy()) <= 1e-10, c
+
+
 def test_replay_is_bitwise_stable_and_buffers_relocate(small_batch):
     batch, rhs, b = small_batch
     u1 = batch.solve(b, check=True).clone()
