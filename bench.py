@@ -157,10 +157,10 @@ def time_steps(torch, fn, steps, warmup, barrier=None):
 
 
 # DRAM bytes (read + write) per DOF of one double-float residual apply, the
-# average of the three launches of a 2D n=9 residual chain, from one ncu
-# capture of the K=512x512 case (511.0 MB per launch at 21.2 M DOF), scaled
+# average of the two launches of a 2D n=9 residual chain, from one ncu
+# capture of the K=512x512 case (529.2 MB per launch at 21.2 M DOF), scaled
 # by the unknowns
-APPLY_DF_TRAFFIC_PER_DOF_2D_N9 = 511.0e6 / 21224449
+APPLY_DF_TRAFFIC_PER_DOF_2D_N9 = 529.2e6 / 21224449
 
 
 def residual_bytes_per_dof(wl):

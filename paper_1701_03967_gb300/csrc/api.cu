@@ -791,6 +791,13 @@ ApplyParams apply_base(fem_fft_plan p, int axis, long long nrhs) {
 //   2D: L u = C_2 (E_1 u) + C_1 (a_2 s_2 A_2 u)
 //   3D: L u = C_3 [C_2 (E_1 u) + C_1 (a_2 s_2 A_2 u)] + C_1 C_2 (a_3 s_3 A_3 u)
 // The temporaries p->tmp hold the partial products.
+// The double-float residual takes the short chain (below): in 3D four
+// launches and seven products instead of six and eight, in 2D two launches
+// instead of three at the same four products; its last launch sums its two
+// products in one set of row sums (apply_kernel_df with SUMT).  Larger 2D
+// solves could take the long chain instead (kShortChainMaxWork).
+constexpr double kShortChainMaxWork = 1e300;   // unknowns x right-hand sides
+
 int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, double* out, const double* b,
                    float* r32, double* norms, cudaStream_t s) {
   const int N = p->N;
@@ -832,6 +839,57 @@ int operator_chain(fem_fft_plan p, const double* u, long long nrhs, int kind, do
     return FEM_FFT_OK;
   }
   double *X = p->tmp[0], *Y = p->tmp[1], *Z = p->tmp[2], *W = p->tmp[3];
+  if (dfr && (N == 3 || (double)nrhs * (double)p->dof <= kShortChainMaxWork)) {
+    // the double-float residual starts on the last axis, so that its last
+    // launch sums two products into r (two launches in 2D, four in 3D):
+    //   X = C_N u, Y = E_N u (E_N = a_N s_N A_N + c C_N), along axis N-1;
+    //   3D: Z = C_2 X, W = a_2 s_2 A_2 X, then W += C_2 Y, along axis 1;
+    //   r = b - (a_1 s_1 A_1 Z' + C_1 W'), along axis 0,
+    // with (Z', W') = (X, Y) in 2D and (Z, W) in 3D
+    const int last = N - 1;
+    auto pair_out = [&](int axis, const double* in, double* o0, int E0, double al0, int E0b, double be0, double* o1,
+                        int E1, double al1, int E1b, double be1) {
+      ApplyParams P = apply_base(p, axis, nrhs);   // o0 = M0 in, o1 = M1 in (one staged input)
+      P.in[0] = in;
+      P.nterm = 2;
+      P.nout = 2;
+      P.out[0] = o0;
+      P.out[1] = o1;
+      set_mat(p, P, 0, E0, al0, E0b, be0);
+      P.t_src[0] = 0; P.t_dst[0] = 0;
+      set_mat(p, P, 1, E1, al1, E1b, be1);
+      P.t_src[1] = 0; P.t_dst[1] = 1;
+      dfify(P);
+      return apply_launch(p, P, s);
+    };
+    if ((e = pair_out(last, u, X, kMatC, 1.0, kMatNone, 0.0, Y, kMatA, s_[last], kMatC, p->c)))
+      return cuda_fail((cudaError_t)e, "apply");
+    const double *F0 = X, *F1 = Y;
+    if (N == 3) {
+      if ((e = pair_out(1, X, Z, kMatC, 1.0, kMatNone, 0.0, W, kMatA, s_[1], kMatNone, 0.0)))
+        return cuda_fail((cudaError_t)e, "apply");
+      ApplyParams P = one(1, Y, W, kMatC, 1.0, kMatNone, 0.0);                 // W += C_2 Y
+      P.addend = W;
+      dfify(P);
+      if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+      F0 = Z;
+      F1 = W;
+    }
+    ApplyParams P = apply_base(p, 0, nrhs);                                   // r = b - (s_1 A_1 F0 + C_1 F1)
+    P.in[0] = F0;
+    P.in[1] = F1;
+    P.nterm = 2;
+    P.nout = 1;
+    P.sum_terms = 1;
+    set_mat(p, P, 0, kMatA, s_[0], kMatNone, 0.0);
+    P.t_src[0] = 0; P.t_dst[0] = 0;
+    set_mat(p, P, 1, kMatC, 1.0, kMatNone, 0.0);
+    P.t_src[1] = 1; P.t_dst[1] = 0;
+    finish(P);
+    dfify(P);
+    if ((e = apply_launch(p, P, s))) return cuda_fail((cudaError_t)e, "apply");
+    return FEM_FFT_OK;
+  }
   {
     ApplyParams P = one(0, u, X, kMatA, s_[0], kMatC, p->c);                   // X = E_1 u
     dfify(P);

@@ -1,5 +1,7 @@
 // Stand-alone operator-apply kernel (one launch per 1D application); the
 // device code is in apply.cuh.
+#include <algorithm>
+
 #include "../../include/femfft.h"
 #include "apply.cuh"
 
@@ -19,26 +21,35 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_kernel(ApplyParams P, 
 // LM: 1 for the lines mode of the contiguous axis, 0 otherwise (compiled
 // apart so that neither pays for the other's index selects: measured 2 % on
 // the 2D n = 9 headline apply)
-template <int NORD, int NOUT, int LM>
+// SUMT: two terms summed into output 0 in one set of row sums
+// (elem_product_df_sum2), one accumulator; compiled for the position tiling
+// only (a summed launch in lines mode takes the two-accumulator kernel).
+template <int NORD, int NOUT, int LM, int SUMT>
 __global__ void __launch_bounds__(kApplyThreads, 4) apply_kernel_df(ApplyParams P, int TW) {
   __shared__ ApplySmemDF<NORD, NOUT, kApplyThreads> S;
   extern __shared__ float2 tiles[];
   apply_stage_mats_df<NORD, NOUT, kApplyThreads>(P, S);
-  apply_block_df<NORD, NOUT, kApplyThreads, true, LM>(P, TW, blockIdx.x, S, tiles);
+  apply_block_df<NORD, NOUT, kApplyThreads, true, LM, SUMT != 0>(P, TW, blockIdx.x, S, tiles);
 }
 
 // dynamic shared memory of a double-float launch, enabling it once per kernel
-template <int NORD, int NOUT, int LM>
+template <int NORD, int NOUT, int LM, int SUMT>
 int launch_apply_df_lm(const ApplyParams& P, int TW, long long blocks, size_t smem, cudaStream_t s) {
-  const int e = ensure_dyn_smem((const void*)apply_kernel_df<NORD, NOUT, LM>, smem);
+  const int e = ensure_dyn_smem((const void*)apply_kernel_df<NORD, NOUT, LM, SUMT>, smem);
   if (e) return e;
-  apply_kernel_df<NORD, NOUT, LM><<<(unsigned)blocks, kApplyThreads, smem, s>>>(P, TW);
+  apply_kernel_df<NORD, NOUT, LM, SUMT><<<(unsigned)blocks, kApplyThreads, smem, s>>>(P, TW);
   return 0;
 }
-template <int NORD, int NOUT>
+template <int NORD>
 int launch_apply_df(const ApplyParams& P, int TW, long long blocks, size_t smem, cudaStream_t s) {
-  if (P.inner == 1 && TW > 1) return launch_apply_df_lm<NORD, NOUT, 1>(P, TW, blocks, smem, s);
-  return launch_apply_df_lm<NORD, NOUT, 0>(P, TW, blocks, smem, s);
+  const bool lines = P.inner == 1 && TW > 1;
+  if (P.sum_terms && !lines) return launch_apply_df_lm<NORD, 1, 0, 1>(P, TW, blocks, smem, s);
+  if (apply_df_nacc(P) <= 1) {
+    if (lines) return launch_apply_df_lm<NORD, 1, 1, 0>(P, TW, blocks, smem, s);
+    return launch_apply_df_lm<NORD, 1, 0, 0>(P, TW, blocks, smem, s);
+  }
+  if (lines) return launch_apply_df_lm<NORD, 2, 1, 0>(P, TW, blocks, smem, s);
+  return launch_apply_df_lm<NORD, 2, 0, 0>(P, TW, blocks, smem, s);
 }
 
 int launch_apply(const ApplyParams& P, cudaStream_t s) {
@@ -49,13 +60,17 @@ int launch_apply(const ApplyParams& P, cudaStream_t s) {
     if (!apply_df_form_ok(P)) return (int)cudaErrorInvalidValue;
     int nin = 0;
     for (int i = 0; i < kApplyMaxIn; ++i) nin += P.in[i] != nullptr;
-    const size_t smem = apply_df_tile_bytes(P.n, TW, kApplyThreads, nin);
+    // one tile per output at least, so that the outputs of blocks narrower
+    // than a warp can leave through the tiles (coalesced) when there are more
+    // outputs than inputs
+    ApplyParams Pc = P;
+    Pc.tile_cap = std::max(nin, P.nout);
+    const size_t smem = apply_df_tile_bytes(P.n, TW, kApplyThreads, Pc.tile_cap);
     int rc = 0;
     switch (P.n) {
 #define FEMFFT_APPLY_DF_CASE(NN)                                                       \
   case NN:                                                                             \
-    rc = P.nout <= 1 ? launch_apply_df<NN, 1>(P, TW, blocks, smem, s)                  \
-                     : launch_apply_df<NN, 2>(P, TW, blocks, smem, s);                 \
+    rc = launch_apply_df<NN>(Pc, TW, blocks, smem, s);                                  \
     if (rc) return rc;                                                                 \
     break;
       FEMFFT_APPLY_DF_CASE(1) FEMFFT_APPLY_DF_CASE(2) FEMFFT_APPLY_DF_CASE(3) FEMFFT_APPLY_DF_CASE(4)

@@ -508,13 +508,77 @@ __device__ __forceinline__ void elem_product_df(const df* Es, const df* Ea, cons
   }
 }
 
+// y = E u + F v for one element: two terms with their own matrices and
+// inputs summed in the same compensated row sums (the even and odd halves
+// of both products advance one set of accumulators), so that the sum costs
+// no second set of n + 1 double-float rows.  Same column order per term as
+// elem_product_df.
+template <int NORD, bool ROW0_ONLY>
+__device__ __forceinline__ void elem_product_df_sum2(const df* Es, const df* Ea, const df* E1, bool has_e1,
+                                                     const float2* col, const df* Fs, const df* Fa, const df* F1,
+                                                     bool has_f1, const float2* colf, int TW, df (&y)[NORD + 1]) {
+  using C = EO<NORD>;
+  constexpr int RR = ROW0_ONLY ? 1 : C::R;
+  float ss[RR], cs[RR], sa[RR], ca[RR];
+#pragma unroll
+  for (int q = 0; q < RR; ++q) ss[q] = cs[q] = sa[q] = ca[q] = 0.0f;
+  df ubt[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const float2* c = t == 0 ? col : colf;
+    const df* Ms = t == 0 ? Es : Fs;
+    const df* Ma = t == 0 ? Ea : Fa;
+    const df u0 = slot_df(c[0]), un = slot_df(c[NORD * TW]);
+    const df ub = df_scale2(df_add(u0, un), 0.5f);
+    const df ub2 = df_scale2(ub, 2.0f);
+    ubt[t] = ub;
+    {
+      const df av = df_sub(u0, un);
+#pragma unroll
+      for (int q = 0; q < RR; ++q) dot2_step(Ma[q * C::P], av, sa[q], ca[q]);
+    }
+#pragma unroll 1
+    for (int j = 1; j < C::P; ++j) {
+      const df uj = slot_df(c[j * TW]), unj = slot_df(c[(NORD - j) * TW]);
+      const df sv = df_sub(df_add(uj, unj), ub2);
+      const df av = df_sub(uj, unj);
+#pragma unroll
+      for (int q = 0; q < RR; ++q) {
+        dot2_step(Ms[q * C::SP + j], sv, ss[q], cs[q]);
+        dot2_step(Ma[q * C::P + j], av, sa[q], ca[q]);
+      }
+    }
+    if (NORD % 2 == 0) {   // the middle node (even n)
+      const df sv = df_sub(slot_df(c[(NORD / 2) * TW]), ub);
+#pragma unroll
+      for (int q = 0; q < RR; ++q) dot2_step(Ms[q * C::SP + C::P], sv, ss[q], cs[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RR; ++q) {
+    const df ts = {ss[q], cs[q]}, ta = {sa[q], ca[q]};
+    df lo = df_add(ts, ta), hi = df_sub(ts, ta);
+    if (has_e1) {
+      lo = df_fma(ubt[0], E1[q], lo);
+      hi = df_fma(ubt[0], E1[NORD - q], hi);
+    }
+    if (has_f1) {
+      lo = df_fma(ubt[1], F1[q], lo);
+      hi = df_fma(ubt[1], F1[NORD - q], hi);
+    }
+    y[q] = lo;
+    if (!ROW0_ONLY && NORD - q != q) y[NORD - q] = hi;
+  }
+}
+
 // Block bx of a double-float apply launch (same tiling as apply_block);
 // tiles: shared memory for the staged inputs (apply_df_tile_bytes).
 // LM: 0 the positions of the other axes per block, 1 lines mode (the caller
 // has checked inner == 1 and TW > 1), 2 decided here (the batched kernel)
-template <int NORD, int NOUT, int NTHREADS, bool NC, int LM = 2>
+template <int NORD, int NOUT, int NTHREADS, bool NC, int LM = 2, bool SUMT = false>
 __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, long long bx,
                                                ApplySmemDF<NORD, NOUT, NTHREADS>& S, float2* tiles) {
+  static_assert(!SUMT || NOUT == 1, "summed terms use one accumulator");
   using C = EO<NORD>;
   constexpr int N1 = C::N1;
   const int K = P.K;
@@ -555,19 +619,37 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
   // term t writes output t (nterm == nout, checked on the host), so each
   // product lands in its accumulator directly
   df acc[NOUT][N1];
-#pragma unroll
-  for (int j = 0; j < NOUT; ++j) {
-    if (valid && j < P.nterm) {
-      elem_product_df<NORD, false>(S.es[j], S.ea[j], S.e1[j], S.has1[j],
-                                   tin[P.t_src[j]] + NORD * te * rstride + tw * cstride, rstride, acc[j]);
+  if constexpr (SUMT) {
+    const int off = NORD * te * rstride + tw * cstride;
+    if (valid) {
+      elem_product_df_sum2<NORD, false>(S.es[0], S.ea[0], S.e1[0], S.has1[0], tin[P.t_src[0]] + off, S.es[1],
+                                        S.ea[1], S.e1[1], S.has1[1], tin[P.t_src[1]] + off, rstride, acc[0]);
     } else {
 #pragma unroll
-      for (int q = 0; q < N1; ++q) acc[j][q] = df{0.0f, 0.0f};
+      for (int q = 0; q < N1; ++q) acc[0][q] = df{0.0f, 0.0f};
     }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NOUT; ++j) {
+      if (valid && j < P.nterm) {
+        elem_product_df<NORD, false>(S.es[j], S.ea[j], S.e1[j], S.has1[j],
+                                     tin[P.t_src[j]] + NORD * te * rstride + tw * cstride, rstride, acc[j]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) acc[j][q] = df{0.0f, 0.0f};
+      }
+    }
+  }
+  if (NOUT == 2 && P.sum_terms && valid) {   // both products into output 0
+#pragma unroll
+    for (int q = 0; q < N1; ++q) acc[0][q] = df_add(acc[0][q], acc[NOUT - 1][q]);
   }
 #pragma unroll
   for (int j = 0; j < NOUT; ++j) S.row0[j][threadIdx.x] = acc[j][0];
   __syncthreads();
+  // outputs this launch writes (one when the terms are summed)
+  constexpr bool kOne = NOUT == 1;
+  const bool one_out = kOne || P.sum_terms;
 
   float rr = 0.0f, bb = 0.0f;
   if (valid) {
@@ -576,6 +658,12 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
       if (te + 1 < TE) {
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) acc[j][NORD] = df_add(acc[j][NORD], S.row0[j][threadIdx.x + estep]);
+      } else if constexpr (SUMT) {
+        const int off = NORD * (te + 1) * rstride + tw * cstride;
+        df y[N1];
+        elem_product_df_sum2<NORD, true>(S.es[0], S.ea[0], S.e1[0], S.has1[0], tin[P.t_src[0]] + off, S.es[1],
+                                         S.ea[1], S.e1[1], S.has1[1], tin[P.t_src[1]] + off, rstride, y);
+        acc[0][NORD] = df_add(acc[0][NORD], y[0]);
       } else {
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) {
@@ -583,7 +671,8 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
             df y[N1];
             elem_product_df<NORD, true>(S.es[j], S.ea[j], S.e1[j], S.has1[j],
                                         tin[P.t_src[j]] + NORD * (te + 1) * rstride + tw * cstride, rstride, y);
-            acc[j][NORD] = df_add(acc[j][NORD], y[0]);
+            if (NOUT == 2 && P.sum_terms) acc[0][NORD] = df_add(acc[0][NORD], y[0]);
+            else acc[j][NORD] = df_add(acc[j][NORD], y[0]);
           }
         }
       }
@@ -594,7 +683,8 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
   // are free now: written per element, stored row by row so that a warp's
   // stores are contiguous (a thread's own rows are TW * inner apart).
   const int orows = NORD * TE;
-  const bool stage_out = TW < 32 && !P.base && !P.addend && !P.out0_f32 && P.nout * orows <= nstaged * rows;
+  const int tile_cap = P.tile_cap > nstaged ? P.tile_cap : nstaged;
+  const bool stage_out = TW < 32 && !P.base && !P.addend && !P.out0_f32 && P.nout * orows <= tile_cap * rows;
   if (stage_out) {
     __syncthreads();   // every staged input has been read
     if (valid) {
@@ -643,7 +733,7 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
     // every row's addend and base values are loaded before the first store:
     // issued inside the store loop, the float loads of a row could not pass
     // the float stores of the rows before it and each row waited on memory
-    if (NOUT == 1 && P.addend) {
+    if (one_out && P.addend) {
       float2 ad[NORD];
 #pragma unroll
       for (int r = 0; r < NORD; ++r) {
@@ -655,7 +745,7 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
       for (int r = 0; r < NORD; ++r) acc[0][r + 1] = df_add(acc[0][r + 1], df{ad[r].x, ad[r].y});
     }
     double bv[NORD];
-    if (NOUT == 1 && P.base) {
+    if (one_out && P.base) {
 #pragma unroll
       for (int r = 0; r < NORD; ++r)
         bv[r] = ld_f64<NC>(&P.base[line + (long long)(NORD * e + min(r, nrow - 1)) * P.inner]);
@@ -668,7 +758,7 @@ __device__ __forceinline__ void apply_block_df(const ApplyParams& P, int TW, lon
       for (int j = 0; j < NOUT; ++j) {
         if (j < P.nout) {
           df v = acc[j][r + 1];
-          if (NOUT == 1 && P.base) {
+          if (one_out && P.base) {
             const df b = split_f64(bv[r]);
             const float rv = df_to_float(df_sub(b, v));
             rr = fmaf(rv, rv, rr);

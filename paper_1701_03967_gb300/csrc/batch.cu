@@ -690,7 +690,7 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
         }
         st.kind = BATCH_APPLY;
         st.ap = op.ap;
-        st.mode = op.ap.nout;
+        st.mode = op.ap.df ? apply_df_nacc(op.ap) : op.ap.nout;
         st.n = op.ap.n;
         const int TW = apply_tile_w(op.ap.inner, op.ap.outer, op.ap.K, kBatchThreads);
         st.TW = TW;

@@ -81,6 +81,12 @@ struct ApplyParams {
   long long bnd_M[kMaxN];
   int bnd_n[kMaxN];              // element orders of all axes (layer depths)
   int hax;                       // host bookkeeping: the operated axis (kernels ignore it)
+  // double-float apply only: 1 = the nterm (two) products are summed into
+  // output 0 (nout = 1); each term keeps its own input t_src[t]
+  int sum_terms;
+  // double-float apply: input tiles of shared memory the launch provides
+  // (0: one per staged input); outputs leave through the tiles when they fit
+  int tile_cap;
 };
 
 // Tile width TW of the apply kernels (a block covers TW positions times
@@ -141,16 +147,23 @@ __host__ __device__ inline ApplyThread apply_decode(long long bx, int tid, int T
   return d;
 }
 
-// The double-float apply handles one or two outputs, term t writing output t;
-// an addend, a residual base or a float32 output only with one output.
+// The double-float apply handles one or two outputs, term t writing output t,
+// or two terms summed into one output (sum_terms); an addend, a residual
+// base or a float32 output only with one output.
 inline bool apply_df_form_ok(const ApplyParams& P) {
-  if (P.dotv || P.nout < 1 || P.nout > 2 || P.nterm != P.nout) return false;
+  if (P.dotv || P.nout < 1 || P.nout > 2 || P.gofs) return false;
   if (P.nout > 1 && (P.addend || P.base || P.out0_f32)) return false;
-  if (P.gofs) return false;
+  if (P.sum_terms) {
+    if (P.nout != 1 || P.nterm != 2) return false;
+    return P.t_dst[0] == 0 && P.t_dst[1] == 0;
+  }
+  if (P.nterm != P.nout) return false;
   for (int t = 0; t < P.nterm; ++t)
     if (P.t_dst[t] != t) return false;
   return true;
 }
+// accumulators (template NOUT) of a double-float launch
+inline int apply_df_nacc(const ApplyParams& P) { return P.sum_terms ? P.nterm : P.nout; }
 int launch_apply(const ApplyParams& P, cudaStream_t s);
 // Dirichlet data (dirichlet.cu): fields extended by the boundary node at
 // each end of every axis (extents M_i + 2, C order, nrhs leading)

@@ -10,6 +10,7 @@ the first failure has already run every other test; it also passes on its own
 in a fresh process."""
 
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -46,17 +47,24 @@ def test_noalloc_apply_matches_plan_apply_twice(case):
         u = torch.from_numpy(synth.normal_batch(2, plan.M, synth.CFG_TEST, 300 + call)).cuda()
         want = plan.apply(u)
         got = torch.full_like(u, float("nan"))
-        torch.cuda.synchronize()
-        free0, _ = torch.cuda.mem_get_info()
-        alloc0 = torch.cuda.memory_allocated()
-        assert _noalloc(L, case, u, got) == 0
-        torch.cuda.synchronize()
-        # the call takes no memory from torch's allocator; after the first
-        # call (which may load the library's device module holding the static
-        # array) none from the driver either
-        assert torch.cuda.memory_allocated() == alloc0
-        if call > 0:
-            assert torch.cuda.mem_get_info()[0] == free0
+        # garbage left by earlier tests must not be collected inside the
+        # measured region (a collection frees tensors and changes the counts)
+        gc.collect()
+        gc.disable()
+        try:
+            torch.cuda.synchronize()
+            free0, _ = torch.cuda.mem_get_info()
+            alloc0 = torch.cuda.memory_allocated()
+            assert _noalloc(L, case, u, got) == 0
+            torch.cuda.synchronize()
+            # the call takes no memory from torch's allocator; after the first
+            # call (which may load the library's device module holding the
+            # static array) none from the driver either
+            assert torch.cuda.memory_allocated() == alloc0
+            if call > 0:
+                assert torch.cuda.mem_get_info()[0] == free0
+        finally:
+            gc.enable()
         rel = float(torch.linalg.norm(got - want) / torch.linalg.norm(want))
         assert rel <= 1e-13, (call, rel)
     plan.close()
