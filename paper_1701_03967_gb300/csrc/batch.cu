@@ -700,6 +700,14 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
           int nin = 0;
           for (int i = 0; i < kApplyMaxIn; ++i) nin += op.ap.in[i] != nullptr;
           st.tile_smem = (int)apply_df_tile_bytes(op.ap.n, TW, kBatchThreads, nin);   // staged input tiles
+          // one tile per output where the CTA has room, so that the outputs of
+          // narrow blocks leave coalesced (as in the stand-alone launch)
+          const int cap = std::max(nin, op.ap.nout);
+          const size_t with_out = apply_df_tile_bytes(op.ap.n, TW, kBatchThreads, cap);
+          if (cap > nin && batch_apply_smem<kMaxOrder>() + with_out <= smem_budget(op.ap.n)) {
+            st.tile_smem = (int)with_out;
+            st.ap.tile_cap = cap;
+          }
         }
         psteps[p].push_back(st);
       }
