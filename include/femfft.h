@@ -104,7 +104,7 @@ int fem_fft_plan_create(fem_fft_plan* out, int N, int n, const int64_t* h_K, con
  * 1D spaces S_{K_i}^{(n_i)} of their own orders.  Axis i then has
  * M_i = n_i K_i - 1 unknowns and its own eigenpairs, transforms and element
  * matrices; the spectral denominators sum the axes' eigenvalues as before.
- * Plans with different orders are not accepted by fem_fft_batch_create.
+ * A batch (fem_fft_batch_create) holding such a plan runs in stream mode only.
  */
 int fem_fft_plan_create_orders(fem_fft_plan* out, int N, const int* h_n, const int64_t* h_K, const double* h_X,
                                const double* h_a, double c, int precision, int64_t max_nrhs, void* stream);
@@ -391,7 +391,11 @@ int fem_fft_apply_noalloc(int N, int n, const int64_t* h_K, const double* h_X, c
  *            cache, else the stand-alone passes' choices
  *   stream   used for the tuning launches; the call synchronises it
  * Returns FEM_FFT_ERR_ARG for a non-mixed or repeated plan or a pencil too
- * large for the persistent kernel's shared memory.
+ * large for the persistent kernel's shared memory.  When some plan has
+ * different element orders on its axes (fem_fft_plan_create_orders) nothing
+ * is recorded: the batch starts in FEM_FFT_BATCH_STREAMS mode (four streams)
+ * and FEM_FFT_BATCH_GRAPH is refused (the batched kernel runs one element
+ * order per launch).
  */
 int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int nprob, const int64_t* h_nrhs,
                          int steps, const char* tune_cache, int tune, void* stream);

@@ -285,7 +285,9 @@ class Plan:
 
 
 class Batch:
-    """Many mixed-precision problems solved by one graph launch.
+    """Many mixed-precision problems solved together: by one graph launch of
+    the recorded work list, or in stream mode (set_mode) by every problem's
+    own plan on a few streams -- the only mode for plans with per-axis orders.
 
     plans: distinct ``Plan`` objects created with precision="mixed" (kept
     alive by the batch); nrhs: right-hand sides per problem (each <= the plan's

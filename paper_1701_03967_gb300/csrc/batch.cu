@@ -435,6 +435,7 @@ struct fem_fft_batch_s {
   std::vector<cudaEvent_t> join;
   cudaEvent_t fork = nullptr;
   std::vector<int> order, stream_of;
+  bool graph_ok = true;   // false: some plan has different orders on its axes (stream mode only)
 };
 
 namespace {
@@ -545,20 +546,21 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
   if (!b) return FEM_FFT_ERR_OOM;
   b->nprob = nprob;
   b->steps = steps;
+  // A plan with different orders on its axes would span launches of the
+  // batched kernel (one per element order): such a batch runs in stream mode
+  // only (no recording, no graph).
+  bool uniform_all = true;
+  for (int p = 0; p < nprob; ++p) {
+    fem_fft_plan pl = plans[p];
+    for (int i = 1; pl && i < pl->N; ++i) uniform_all = uniform_all && pl->nax[i] == pl->nax[0];
+  }
+  b->graph_ok = uniform_all;
   // 1. record every problem's solve chain with placeholder field addresses
   int64_t off = 0;
   std::vector<std::vector<RecordedOp>> chains(nprob);
   std::vector<double> work(nprob);
   for (int p = 0; p < nprob; ++p) {
     fem_fft_plan pl = plans[p];
-    bool uniform = pl != nullptr;
-    for (int i = 1; pl && i < pl->N; ++i) uniform = uniform && pl->nax[i] == pl->nax[0];
-    if (pl && !uniform) {
-      // the batched kernel runs every step of a problem in the launch of its
-      // element order; a plan with several orders would span launches
-      free_batch(b);
-      return batch_fail(FEM_FFT_ERR_ARG, "batch: plans must have one element order on every axis");
-    }
     if (!pl || pl->precision != FEM_FFT_MIXED || h_nrhs[p] < 1 || h_nrhs[p] > pl->max_nrhs) {
       free_batch(b);
       return batch_fail(FEM_FFT_ERR_ARG, "batch: every plan must be mixed precision with nrhs <= max_nrhs");
@@ -572,7 +574,7 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
     b->offset.push_back(off);
     const double* tb = reinterpret_cast<const double*>(kTagB + (uintptr_t)off * sizeof(double));
     double* tu = reinterpret_cast<double*>(kTagU + (uintptr_t)off * sizeof(double));
-    int rc = record_mixed_solve(pl, tb, tu, h_nrhs[p], steps, &chains[p]);
+    int rc = uniform_all ? record_mixed_solve(pl, tb, tu, h_nrhs[p], steps, &chains[p]) : FEM_FFT_OK;
     if (rc) {
       free_batch(b);
       return batch_fail(rc, "batch: recording a solve chain failed");
@@ -583,6 +585,15 @@ int fem_fft_batch_create(fem_fft_batch* out, const fem_fft_plan* plans, int npro
   b->total_len = off;
   b->plans.assign(plans, plans + nprob);
   b->work = work;
+  if (!uniform_all) {
+    const int rc = fem_fft_batch_set_mode(b, FEM_FFT_BATCH_STREAMS, 4);
+    if (rc) {
+      free_batch(b);
+      return rc;
+    }
+    *out = b;
+    return FEM_FFT_OK;
+  }
   // 2. tile shapes and radix schedules
   std::map<TuneKey, PassParams> keys;
   for (auto& ch : chains)
@@ -849,6 +860,8 @@ int fem_fft_batch_hold_step(fem_fft_batch b, int64_t step) {
 
 int fem_fft_batch_set_mode(fem_fft_batch b, int mode, int nstreams) {
   if (!b || (mode != FEM_FFT_BATCH_GRAPH && mode != FEM_FFT_BATCH_STREAMS)) return FEM_FFT_ERR_ARG;
+  if (mode == FEM_FFT_BATCH_GRAPH && !b->graph_ok)
+    return batch_fail(FEM_FFT_ERR_ARG, "batch: plans with per-axis orders run in stream mode only");
   if (mode == FEM_FFT_BATCH_STREAMS && (nstreams < 1 || nstreams > 64)) return FEM_FFT_ERR_ARG;
   cudaDeviceSynchronize();   // no solve of either mode may still use the streams
   drop_streams(b);

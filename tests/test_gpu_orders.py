@@ -33,6 +33,10 @@ def _relmax(x, y):
     return float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
 
 
+def _prob(case):
+    return osolve.Problem(case["n"], case["K"], case["X"], case["a"], case["c"])
+
+
 def _plan(case, precision, max_nrhs=2):
     from paper_1701_03967_gb300 import Plan
     return Plan(case["n"], case["K"], case["X"], case["a"], case["c"], precision, max_nrhs=max_nrhs)
@@ -103,9 +107,22 @@ def test_dirichlet_polynomial_with_per_axis_orders(case):
     assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
 
 
-def test_batch_rejects_per_axis_orders():
+def test_batch_of_per_axis_order_plans_runs_in_stream_mode():
+    """A batch holding plans with per-axis orders solves every problem by its
+    own plan on the batch's streams (the graph launch, one element order per
+    launch, is refused), to the mixed bar against the oracle."""
     from paper_1701_03967_gb300 import Batch, FemFftError
-    plan = _plan(CASES[0], "mixed", 1)
+    cases = [CASES[0], CASES[1], dict(n=4, K=(16, 8), X=(1.0, 1.0), a=(1.0, 2.0), c=0.5)]
+    plans = [_plan(c, "mixed", 2) for c in cases]
+    batch = Batch(plans, [2, 1, 2], tune=False)
+    assert batch.n_steps == 0
     with pytest.raises(FemFftError):
-        Batch([plan], [1], tune=False)
-    plan.close()
+        batch.set_mode("graph")
+    rhs = [synth.normal_batch(r, _prob(c).M, synth.CFG_TEST, 700 + i) for i, (c, r) in enumerate(zip(cases, [2, 1, 2]))]
+    u = batch.solve(batch.pack(rhs))
+    torch.cuda.synchronize()
+    for c, bp, up in zip(cases, rhs, batch.views(u)):
+        want = osolve.solve(_prob(c), bp)
+        assert _rel(up.cpu().numpy(), want) <= 1e-10, c
+    for pl in plans:
+        pl.close()
