@@ -387,6 +387,7 @@ def run_other_workloads(torch, args, barrier):
     del gx, fb, work, ud
     torch.cuda.empty_cache()
     res["transform_1d_n5"] = transform_sweep(torch, args, barrier, g)
+    res["transform_2d_n5_K4096"] = long_strided_transforms(torch, args, barrier, g)
     return res
 
 
@@ -430,6 +431,29 @@ def transform_sweep(torch, args, barrier, g, n=5):
         pl.close()
         del y, c, w
     return out
+
+
+def long_strided_transforms(torch, args, barrier, g, n=5, K=4096):
+    """Float64 transforms of a 2D field with pencils longer than one CTA holds
+    on both axes (n = 5, K = 4096 x 4096, 419 M unknowns): the strided axis 0
+    and the contiguous axis 1 both take the global four-step path; per
+    transform, with the mass round trip inverse(forward(calC y)) = y."""
+    from paper_1701_03967_gb300 import Plan
+    steps = max(2, args.steps // 4)
+    pl = Plan(n, (K, K), None, None, 0.0, precision="fp64")
+    y = torch.randn(tuple(pl.M), dtype=torch.float64, device="cuda", generator=g)
+    c = torch.empty_like(y)
+    w = torch.empty_like(y)
+    ms_f = time_steps(torch, lambda: pl.forward(y, out=c), steps, args.warmup, barrier)
+    ms_i = time_steps(torch, lambda: pl.inverse(c, out=w), steps, args.warmup, barrier)
+    pl.forward(pl.apply_mass(y), out=c)
+    pl.inverse(c, out=w)
+    rel = float(torch.linalg.vector_norm(w - y) / torch.linalg.vector_norm(y))
+    dof = pl.dof
+    pl.close()
+    del y, c, w
+    return {"dof": dof, "forward_ms": ms_f, "inverse_ms": ms_i, "forward_dof_per_s": dof / (ms_f * 1e-3),
+            "inverse_dof_per_s": dof / (ms_i * 1e-3), "mass_roundtrip_rel_err": rel}
 
 
 def workload_config(wl, args, ws):
