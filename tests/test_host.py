@@ -92,3 +92,20 @@ def test_noalloc_rejects_oversized_and_invalid_problems_without_a_device_call():
     assert call(2, 2, (16, 16), c=-2.0 * np.pi ** 2) == -1  # L not positive definite
     assert call(2, 2, (16, 15)) == -1                      # K must be 2^p 3^q, p >= 1
     assert call(2, 2, (16, 16)) == 0                       # valid, nrhs = 0: a no-op
+
+
+def test_entry_points_reject_bad_arguments_without_a_device_call():
+    """Argument checks that return before any CUDA call: null handles, negative
+    counts, unknown modes (so they run without a GPU)."""
+    import ctypes
+    from paper_1701_03967_gb300 import _lib
+    L = _lib.lib()
+    buf = (ctypes.c_double * 4)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.fem_fft_divide_check(p, p, p, p, -1, None) == -1
+    assert L.fem_fft_divide_check(None, p, p, p, 4, None) == -1
+    assert L.fem_fft_divide_check(None, None, None, None, 0, None) == 0
+    assert L.fem_fft_batch_set_mode(None, 1, 4) == -1
+    assert L.fem_fft_solve_host(None, p, p, 1, None) == -1
+    assert L.fem_fft_host_wait(None, None) == -1
+    assert L.fem_fft_batch_solve(None, p, p, None) == -1
