@@ -9,10 +9,12 @@
 // chain of 1D applications along the axes, e.g. in 2D
 //     w = (a_1 s_1 calA_1 + c calC_1) u (axis 1), t = a_2 s_2 calA_2 u (axis 2),
 //     L u = calC_2 w + calC_1 t.
-// The stiffness factor of every term is applied to u itself and the mass
-// factors afterwards: a stiffness applied to an intermediate that carries
-// white rounding noise (such as calC_2 u) would amplify that noise by
-// ~4 h^-2 |A| and floor the refinement at ~6e-9 (2D, n = 9, K = 1024).
+// In the float64 chains the stiffness factor of every term is applied to u
+// itself and the mass factors afterwards: a float64 stiffness applied to an
+// intermediate that carries rounding noise (such as calC_2 u) amplified
+// that noise by ~4 h^-2 |A| and floored the refinement at ~6e-9 (2D, n = 9,
+// K = 1024).  The double-float residual's shorter chain applies stiffness
+// factors to double-float mass products; see operator_chain in api.cu.
 // One thread computes the outputs of one element for all outputs of the
 // launch; inputs are read through the read-only cache (along strided axes the
 // threads of a warp cover consecutive positions of the contiguous axis).
