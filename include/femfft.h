@@ -172,7 +172,7 @@ int fem_fft_apply_mass(fem_fft_plan plan, const double* d_u, double* d_b, int64_
  * cannot be had.  Asynchronous on stream.  A MIXED solve of the corrected
  * right-hand side (which carries the boundary layer of the data) can need a
  * third refinement step (fem_fft_set_refinement): on the 2D n = 9 K = 1024
- * problem two steps left 1.8e-10, three 2.2e-13.
+ * problem two steps left 1.7e-10, three 3.1e-13.
  */
 int fem_fft_dirichlet_rhs(fem_fft_plan plan, const double* d_g, double* d_b, int64_t nrhs, void* stream);
 

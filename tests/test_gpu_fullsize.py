@@ -62,8 +62,8 @@ def test_fullsize_dirichlet_data_reproduce_a_polynomial(precision, tol):
     -sum a_i u_ii + c u is exact with (n+1)-point Gauss).  Relative L2 error
     against the nodal values.  The mixed plan runs three refinement steps:
     the corrected right-hand side carries the boundary layer of the data, and
-    two steps measured 1.8e-10 (three: 2.2e-13; a smooth solution with zero
-    boundary values reaches 7e-13 in the default two)."""
+    two steps measured 1.7e-10 (three: 3.1e-13; a smooth solution with zero
+    boundary values reaches 1.4e-13 in the default two)."""
     from oracle import harness
     from paper_1701_03967_gb300 import Plan
     wl = WORKLOADS[0][1]
