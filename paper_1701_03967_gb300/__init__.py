@@ -142,7 +142,7 @@ class Plan:
         L^{-1} (f - L_full G) (Section 4 with non-zero Dirichlet data).  A
         mixed plan may need ``set_refinement(0.0, 3)`` here: the corrected
         right-hand side carries the boundary layer of the data (2D n=9
-        K=1024: two steps 1.8e-10, three 2.2e-13)."""
+        K=1024: two steps 1.7e-10, three 3.1e-13)."""
         rhs = f.clone()
         self.dirichlet_rhs(g, rhs, stream=stream)
         return self.solve(rhs, out=out, stream=stream)
